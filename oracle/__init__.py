@@ -1,0 +1,181 @@
+"""CPU oracle for positive Datalog (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  It shares no code with the GPU library; the product never
+loads it.
+
+The evaluator itself is plain C (``oracle.c``): a semi-naive engine with left-deep,
+hash-indexed nested-loop joins (paper Section 2), and a brute-force naive T_P used to
+pin it.  This module compiles it with gcc, loads it with ctypes and converts between
+numpy arrays and the C calls.
+
+Program format (plain data, built by the caller):
+
+* ``relations``: ``{name: arity}``
+* ``facts``: ``{name: (rows, arity) uint32 array}``
+* ``rules``: list of ``(head, body)`` where ``head`` is an atom and ``body`` a list of
+  atoms; an atom is ``(relation_name, [term, ...])``; a term is a ``str`` (variable)
+  or an ``int`` (constant).  A rule may carry a third item, a variable order, which is
+  ignored: the oracle's result does not depend on one.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from .partition import decode_unit, work_slices  # noqa: F401  (re-exported)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MODES = {"seminaive": 0, "naive_strata": 1, "naive_global": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` next to it (gcc, -O2, no -march)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            lib.orc_create.restype = ctypes.c_void_p
+            lib.orc_destroy.argtypes = [ctypes.c_void_p]
+            lib.orc_error.restype = ctypes.c_char_p
+            lib.orc_error.argtypes = [ctypes.c_void_p]
+            lib.orc_relation.argtypes = [ctypes.c_void_p, ctypes.c_uint32]
+            lib.orc_add_facts.argtypes = [ctypes.c_void_p, ctypes.c_int, u32p, ctypes.c_uint64]
+            lib.orc_add_rule.argtypes = [ctypes.c_void_p, ctypes.c_int, u32p, u32p, ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_int32), u32p, u32p]
+            lib.orc_run.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.orc_count.restype = ctypes.c_uint64
+            lib.orc_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.orc_fetch.argtypes = [ctypes.c_void_p, ctypes.c_int, u32p]
+            lib.orc_num_strata.restype = ctypes.c_uint32
+            lib.orc_num_strata.argtypes = [ctypes.c_void_p]
+            lib.orc_stratum.argtypes = [ctypes.c_void_p, ctypes.c_uint32, u32p, u32p, u32p]
+            _lib = lib
+    return _lib
+
+
+def _u32(a) -> ctypes.POINTER(ctypes.c_uint32):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+class Result:
+    """Per-relation sorted distinct rows and the strata with their round counts."""
+
+    def __init__(self, relations: dict, strata: list):
+        self.relations = relations          # name -> (rows, arity) uint32, sorted, distinct
+        self.strata = strata                # [(sorted relation names, rounds), ...] in evaluation order
+
+    def rounds_of(self, name: str) -> int:
+        for rels, r in self.strata:
+            if name in rels:
+                return r
+        raise KeyError(name)
+
+
+def evaluate(relations: dict, facts: dict, rules: list, mode: str = "seminaive") -> Result:
+    """Run a program to its least fixpoint and return every relation."""
+    lib = _load()
+    h = lib.orc_create()
+    try:
+        names = list(relations)
+        rid = {}
+        for name in names:
+            r = lib.orc_relation(h, int(relations[name]))
+            if r < 0:
+                raise OracleError(lib.orc_error(h).decode())
+            rid[name] = r
+        for name, rows in facts.items():
+            rows = np.ascontiguousarray(rows, dtype=np.uint32).reshape(-1, relations[name])
+            if lib.orc_add_facts(h, rid[name], _u32(rows), rows.shape[0]) != 0:
+                raise OracleError(lib.orc_error(h).decode())
+        for rule in rules:
+            head, body = rule[0], rule[1]   # a third item (a variable order) is ignored
+            def enc(terms, rel):
+                if len(terms) != relations[rel]:
+                    raise OracleError(f"arity mismatch in atom {rel}{tuple(terms)}")
+                kinds, vals = [], []
+                for t in terms:
+                    if isinstance(t, str):
+                        kinds.append(0)
+                        vals.append(var_ids.setdefault(t, len(var_ids)))
+                    else:
+                        kinds.append(1)
+                        vals.append(int(t))
+                return kinds, vals
+            var_ids: dict = {}
+            bk, bv, brels = [], [], []
+            for rel, terms in body:
+                k, v = enc(terms, rel)
+                bk += k
+                bv += v
+                brels.append(rid[rel])
+            hk, hv = enc(head[1], head[0])
+            arr = lambda x: np.asarray(x, dtype=np.uint32)  # noqa: E731
+            hk_a, hv_a, bk_a, bv_a = arr(hk), arr(hv), arr(bk), arr(bv)
+            br_a = np.asarray(brels, dtype=np.int32)
+            ok = lib.orc_add_rule(h, rid[head[0]], _u32(hk_a), _u32(hv_a), len(body),
+                                  br_a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  _u32(bk_a), _u32(bv_a))
+            if ok < 0:
+                raise OracleError(lib.orc_error(h).decode())
+        if lib.orc_run(h, MODES[mode]) != 0:
+            raise OracleError(lib.orc_error(h).decode())
+        out = {}
+        for name in names:
+            n = lib.orc_count(h, rid[name])
+            rows = np.empty((n, relations[name]), dtype=np.uint32)
+            if n:
+                lib.orc_fetch(h, rid[name], _u32(rows))
+            out[name] = rows
+        strata = []
+        for s in range(lib.orc_num_strata(h)):
+            rounds = ctypes.c_uint32()
+            nrels = ctypes.c_uint32()
+            rels = np.empty(len(names), dtype=np.uint32)
+            lib.orc_stratum(h, s, ctypes.byref(rounds), _u32(rels), ctypes.byref(nrels))
+            strata.append((sorted(names[i] for i in rels[: nrels.value]), rounds.value))
+        return Result(out, strata)
+    finally:
+        lib.orc_destroy(h)
+
+
+def tuple_digest(rows: np.ndarray) -> tuple:
+    """Order-independent digest of a set of rows: (count, sum mod 2^64, xor) of a 64-bit
+    hash of each row.  Row hash: h = 0x243F6A8885A308D3; for column j with value v,
+    h = mix(h ^ (v + 0x9E3779B97F4A7C15 * (j + 1))), mix being the splitmix64 finaliser.
+    Written here from that definition with Python integers, row by row."""
+    M = (1 << 64) - 1
+    s = 0
+    x = 0
+    for row in np.asarray(rows, dtype=np.uint64).tolist():
+        h = 0x243F6A8885A308D3
+        for j, v in enumerate(row):
+            z = (h ^ ((v + 0x9E3779B97F4A7C15 * (j + 1)) & M)) & M
+            z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+            z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+            h = z ^ (z >> 31)
+        s = (s + h) & M
+        x ^= h
+    return (len(rows), s, x)

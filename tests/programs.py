@@ -1,0 +1,40 @@
+"""Datalog programs used by the tests and the benchmark, as plain data.
+
+A rule is (head, body, variable_order); an atom is (relation, [terms]); a term is a
+str (variable) or an int (constant).  The oracle ignores the variable order."""
+
+TC = [
+    (("Reach", ["x", "y"]), [("E", ["x", "y"])], ["x", "y"]),
+    (("Reach", ["x", "z"]), [("Reach", ["x", "y"]), ("E", ["y", "z"])], ["x", "y", "z"]),
+]
+TC_RELS = {"E": 2, "Reach": 2}
+
+TRI = [
+    (("Tri", ["x", "y", "z"]), [("E", ["x", "y"]), ("E", ["y", "z"]), ("E", ["x", "z"])], ["x", "y", "z"]),
+]
+TRI_RELS = {"E": 2, "Tri": 3}
+
+Q4 = [
+    (("Q4", ["w", "x", "y", "z"]),
+     [("E", ["w", "x"]), ("E", ["w", "y"]), ("E", ["w", "z"]),
+      ("E", ["x", "y"]), ("E", ["x", "z"]), ("E", ["y", "z"])],
+     ["w", "x", "y", "z"]),
+]
+Q4_RELS = {"E": 2, "Q4": 4}
+
+# Reach + Tri over one edge relation (the small plain-method workload).
+TC_TRI = TC + TRI
+TC_TRI_RELS = {"E": 2, "Reach": 2, "Tri": 3}
+
+# Andersen-style points-to (Load is (v, w, f), Store is (v, f, w)).
+POINTS_TO = [
+    (("VPT", ["v", "h"]), [("New", ["v", "h"])], ["v", "h"]),
+    (("VPT", ["v", "h"]), [("Assign", ["v", "w"]), ("VPT", ["w", "h"])], ["w", "v", "h"]),
+    (("FPT", ["h1", "f", "h2"]),
+     [("Store", ["v1", "f", "v2"]), ("VPT", ["v1", "h1"]), ("VPT", ["v2", "h2"])],
+     ["v1", "h1", "f", "v2", "h2"]),
+    (("VPT", ["v", "h2"]),
+     [("Load", ["v", "w", "f"]), ("VPT", ["w", "h1"]), ("FPT", ["h1", "f", "h2"])],
+     ["w", "h1", "f", "v", "h2"]),
+]
+POINTS_TO_RELS = {"New": 2, "Assign": 2, "Load": 3, "Store": 3, "VPT": 2, "FPT": 3}
