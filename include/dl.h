@@ -1,0 +1,236 @@
+/*
+ * dl.h -- C ABI of the GB300 semi-naive WCOJ Datalog library (libdlgpu.so).
+ *
+ * The library evaluates positive Datalog programs (Horn clauses
+ * Head(...) <- Body1(...), ..., Bodyn(...), paper Section 2 "Datalog") to their least
+ * fixpoint by semi-naive evaluation (Section 2, Delta_{i+1} = pi(Delta_i |x| ...) \ Full),
+ * stratum by stratum (Section 2: SCCs of the relation dependency graph, each run to its
+ * own fixpoint and then read-only).  Every rule body is joined attribute at a time, a
+ * worst-case-optimal join in the sense of Section 2 "Join Processing and Worst-Case
+ * Optimal Join": under a variable order (x1..xm) the candidates of x_i are the
+ * intersection of the sorted projections of every atom that mentions x_i, restricted by
+ * the prefix bound so far.  Relations are flat, lexicographically sorted uint32 column
+ * arrays (Section 4, flat SoA storage); join output is allocated by a count pass, a device
+ * prefix scan and a write pass (Section 4, imperative 1; Algorithm 1).
+ *
+ * Conventions for every call:
+ *  - Every function returns an int status; DL_OK (0) means success.  On failure the
+ *    engine keeps a one-line description, readable through dl_last_error().  No C++
+ *    exception crosses this boundary.
+ *  - An engine handle is single-threaded: calls on one handle must not overlap.
+ *  - Values are uint32.  Row counts, offsets and sizes are uint64.
+ *  - Host pointers are only read during the call (the library copies what it keeps);
+ *    device pointers returned by the library stay owned by the engine.
+ *  - All device work is issued on the engine's stream (dl_config.stream).  Calls that
+ *    return host-visible results synchronise that stream before returning.
+ */
+#ifndef DL_H
+#define DL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define DL_OK 0
+#define DL_ERR_ARG 1          /* an argument is invalid (bad id, arity mismatch, unsafe rule, ...) */
+#define DL_ERR_UNSUPPORTED 2  /* valid Datalog that this GPU path does not evaluate (see dl_rule_add) */
+#define DL_ERR_CAPACITY 3     /* the device-memory budget would be exceeded; state is unchanged */
+#define DL_ERR_CUDA 4         /* a CUDA runtime call failed; the engine must be destroyed */
+#define DL_ERR_TIMEOUT 5      /* reserved: a bounded device-side wait gave up */
+#define DL_ERR_STATE 6        /* the call is not valid in the engine's current state */
+
+/* ------------------------------------------------------------------ limits */
+#define DL_MAX_ARITY 8        /* columns per relation */
+#define DL_MAX_VARS 12        /* distinct variables per rule */
+#define DL_MAX_BODY 8         /* atoms per rule body */
+#define DL_MAX_STRATA 64      /* strata reported in dl_stats (more may exist) */
+
+/* dl_config.flags */
+#define DL_FLAG_NAIVE_ROOTS 0x1u  /* A/B baseline: one root key per work group, no histogram split
+                                     (the naive assignment ablated in Section 7.3) */
+#define DL_FLAG_DEBUG_CHECKS 0x2u /* re-verify sortedness/uniqueness of every index after each round */
+
+typedef struct dl_engine dl_engine;
+typedef uint32_t dl_rel_id;
+typedef uint32_t dl_rule_id;
+
+/* Optional allocator: when alloc is set, every device buffer of the engine comes from
+ * alloc(bytes, stream, user) and is returned through free(ptr, bytes, stream, user).
+ * Returned pointers must be 256-byte aligned device memory.  NULL from alloc means out of
+ * memory (reported as DL_ERR_CAPACITY). */
+typedef void* (*dl_alloc_fn)(uint64_t bytes, void* stream, void* user);
+typedef void (*dl_free_fn)(void* ptr, uint64_t bytes, void* stream, void* user);
+
+typedef struct dl_config {
+    int device;               /* CUDA device ordinal; -1 = the calling thread's current device */
+    void* stream;             /* cudaStream_t to issue all work on; NULL = engine-owned stream */
+    uint64_t arena_bytes;     /* device-memory budget; 0 = 90% of free memory at creation */
+    dl_alloc_fn alloc;        /* optional, see above (both or neither of alloc/free) */
+    dl_free_fn free;
+    void* alloc_user;
+    uint32_t flags;           /* DL_FLAG_* */
+    uint32_t tile_units;      /* join work units per CTA tile; 0 = default (4096) */
+} dl_config;
+
+/* ------------------------------------------------------------------ engine */
+
+/* Create an engine.  cfg may be NULL (all defaults).  *out receives the handle.
+ * Errors: DL_ERR_ARG (bad config), DL_ERR_CUDA (no device / context creation failed). */
+int dl_engine_create(const dl_config* cfg, dl_engine** out);
+
+/* Destroy an engine and free every device buffer it owns.  NULL is ignored. */
+void dl_engine_destroy(dl_engine* e);
+
+/* Description of the last failure on this engine ("" if none).  The string is owned by
+ * the engine and valid until its next call. */
+const char* dl_last_error(const dl_engine* e);
+
+/* Library version string, e.g. "1.0.0". */
+const char* dl_version(void);
+
+/* ---------------------------------------------------------------- relations */
+
+/* Declare a relation of the given arity (1..DL_MAX_ARITY); all columns are uint32
+ * (Section 4: flat sorted uint32 columns).  Names are unique per engine.
+ * Errors: DL_ERR_ARG (arity out of range, duplicate or empty name), DL_ERR_STATE (after
+ * dl_fixpoint has begun using the relation set). */
+int dl_relation_create(dl_engine* e, const char* name, uint32_t arity, dl_rel_id* out);
+
+/* Relation sinks.  DL_SINK_STORE (default) materialises the relation.  DL_SINK_COUNT keeps
+ * only the number of distinct derived tuples and an order-independent digest of them
+ * (dl_fetch_digest); it is for outputs too large to hold (e.g. 4-cliques of a large
+ * graph).  A count sink must not appear in any rule body, and must be derived by exactly
+ * one rule whose head lists each body variable exactly once (then every binding the join
+ * enumerates is a distinct tuple and no deduplication is needed).
+ * Errors: DL_ERR_ARG (bad id or sink), DL_ERR_UNSUPPORTED (rules violate the above; checked
+ * at dl_fixpoint). */
+#define DL_SINK_STORE 0u
+#define DL_SINK_COUNT 1u
+int dl_relation_set_sink(dl_engine* e, dl_rel_id rel, uint32_t sink);
+
+/* Add facts to a relation from HOST memory.  cols[j] points to nrows uint32 values of
+ * column j (column-major, one pointer per column).  Set semantics: duplicates, also
+ * against facts already loaded, are dropped (Section 2: relations are sets).  Facts may be
+ * loaded into any relation before dl_fixpoint; facts loaded into a derived relation are
+ * part of its stratum's first-round delta.  The caller keeps ownership of the buffers.
+ * Errors: DL_ERR_ARG (bad id, NULL column with nrows > 0), DL_ERR_CAPACITY, DL_ERR_STATE
+ * (the relation is a count sink). */
+int dl_load_facts(dl_engine* e, dl_rel_id rel, const uint32_t* const* cols, uint64_t nrows);
+
+/* Same, from one HOST row-major buffer of nrows * arity values. */
+int dl_load_facts_rows(dl_engine* e, dl_rel_id rel, const uint32_t* rows, uint64_t nrows);
+
+/* Same, from DEVICE memory (column pointers on the engine's device); the data are copied,
+ * the caller keeps ownership.  The copy is ordered on the engine's stream. */
+int dl_load_facts_device(dl_engine* e, dl_rel_id rel, const uint32_t* const* dcols, uint64_t nrows);
+
+/* Remove every tuple of a relation (facts and derived tuples).  Rules are kept. */
+int dl_relation_clear(dl_engine* e, dl_rel_id rel);
+
+/* ------------------------------------------------------------------- rules */
+
+#define DL_TERM_VAR 0u
+#define DL_TERM_CONST 1u
+typedef struct dl_term {
+    uint32_t kind;            /* DL_TERM_VAR or DL_TERM_CONST */
+    uint32_t id;              /* variable id (any uint32 < 1024) or the constant value */
+} dl_term;
+
+typedef struct dl_atom {
+    dl_rel_id rel;
+    uint32_t arity;           /* must equal the relation's arity */
+    const dl_term* terms;     /* arity terms */
+} dl_atom;
+
+/* Add the rule head <- body[0], ..., body[nbody-1] (Section 2, Horn clause) with the join
+ * variable order var_order[0..nvars) (Section 2, WCOJ: "fix a global variable order
+ * (x1..xm)"; it fixes the attribute order of the join, not a filter on values).
+ * var_order must be a permutation of the distinct body variables.  Every head variable
+ * must occur in the body (range restriction).
+ * GPU path limits: constants in body atoms, and a variable repeated within one body atom,
+ * return DL_ERR_UNSUPPORTED; head constants are allowed.
+ * Errors: DL_ERR_ARG (bad ids, arity mismatch, unsafe head, bad order, nbody == 0 or
+ * > DL_MAX_BODY, more than DL_MAX_VARS variables), DL_ERR_UNSUPPORTED, DL_ERR_STATE. */
+int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody,
+                const uint32_t* var_order, uint32_t nvars, dl_rule_id* out);
+
+/* ------------------------------------------------------------------ fixpoint */
+
+typedef struct dl_stats {
+    uint32_t nstrata;                        /* strata evaluated (relations derived by rules) */
+    uint32_t rounds[DL_MAX_STRATA];          /* rounds of each stratum, in evaluation order */
+    uint32_t stratum_first_rel[DL_MAX_STRATA]; /* smallest relation id of each stratum */
+    uint32_t total_rounds;
+    uint64_t join_rows;        /* rows written by the join materialize passes (before dedup) */
+    uint64_t count_rows;       /* bindings counted into DL_SINK_COUNT relations */
+    uint64_t delta_rows;       /* new tuples merged over all rounds */
+    uint64_t peak_bytes;       /* peak device bytes held by the engine during the call */
+    uint64_t kernel_launches;  /* kernels launched by the call */
+    double ms_total;           /* wall time of the call */
+    double ms_join;            /* device time of histogram + count + scan + materialize */
+    double ms_sort;            /* device time of delta radix sorts */
+    double ms_dedup;           /* device time of dedup + anti-join (compute delta) */
+    double ms_merge;           /* device time of merges and index rebuilds */
+} dl_stats;
+
+/* Evaluate all rules to the least fixpoint (semi-naive, Jacobi rounds: every rule of a
+ * round reads the state at the round's start).  Round 1 of a stratum evaluates its
+ * non-recursive rules; rounds t >= 2 evaluate one delta variant per recursive body atom;
+ * a stratum stops at the first round with an empty delta, and its round count includes
+ * that round (a stratum without recursive rules takes 1 round).  stats may be NULL.
+ * May be called again after more facts are loaded; it then continues from the current
+ * contents (all relations are treated as loaded facts).
+ * Errors: DL_ERR_CAPACITY (the budget would be exceeded; relations keep the state of the
+ * last completed round), DL_ERR_UNSUPPORTED, DL_ERR_CUDA. */
+int dl_fixpoint(dl_engine* e, dl_stats* stats);
+
+/* Stratum details after dl_fixpoint: relation ids of stratum s (ascending) into
+ * rels[0..cap), their number in *nrels, and its round count. */
+int dl_stratum_info(dl_engine* e, uint32_t s, dl_rel_id* rels, uint32_t cap, uint32_t* nrels,
+                    uint32_t* rounds);
+
+/* --------------------------------------------------------------------- fetch */
+
+/* Number of tuples currently in a relation (DL_SINK_COUNT: the counted tuples). */
+int dl_relation_size(dl_engine* e, dl_rel_id rel, uint64_t* nrows);
+
+/* Copy a relation to HOST memory, column-major: cols_out[j] receives column j.  Rows are
+ * distinct and sorted ascending lexicographically over columns 0..arity-1 (unsigned).
+ * Two-call pattern: with cols_out == NULL only *nrows_out is written.  cap_rows is the
+ * capacity of each column buffer.
+ * Errors: DL_ERR_ARG (cap_rows < size), DL_ERR_STATE (count sink). */
+int dl_fetch(dl_engine* e, dl_rel_id rel, uint32_t* const* cols_out, uint64_t cap_rows,
+             uint64_t* nrows_out);
+
+/* Same into DEVICE buffers on the engine's device (ordered on the engine's stream). */
+int dl_fetch_device(dl_engine* e, dl_rel_id rel, uint32_t* const* dcols_out, uint64_t cap_rows,
+                    uint64_t* nrows_out);
+
+/* Order-independent digest of a relation: *count = number of tuples, digest[0] = sum mod
+ * 2^64 and digest[1] = xor of a 64-bit hash of every tuple.  Tuple hash: h starts at
+ * 0x243F6A8885A308D3; for column j with value v, h = mix(h ^ (v + 0x9E3779B97F4A7C15*(j+1)))
+ * where mix is the splitmix64 finaliser.  Works for stored relations and count sinks. */
+int dl_fetch_digest(dl_engine* e, dl_rel_id rel, uint64_t* count, uint64_t digest[2]);
+
+/* ------------------------------------------------------------- host helpers */
+
+/* Root-level work partition of Algorithm 2 / Figure 2, the same routine the join kernels
+ * run: given the inclusive prefix sums C[0..K) of per-key work, group b of p takes flat
+ * units [b*ceil(T/p), min((b+1)*ceil(T/p), T)) with T = C[K-1]; its first key is the first
+ * k with C[k] > start.  Writes first_key[b] and start_unit[b] (global unit index) for every
+ * b < p.  Host-callable; needs no GPU. */
+int dl_partition_slices(const uint64_t* C, uint64_t K, uint32_t p, uint64_t* first_key,
+                        uint64_t* start_unit);
+
+/* Decode one flat unit g into (key, i1, i2) with local = g - C[key-1],
+ * i1 = local / d2[key], i2 = local % d2[key] (Section 5, the decode formula). Host-callable. */
+int dl_decode_unit(const uint64_t* C, const uint64_t* d2, uint64_t K, uint64_t g, uint64_t* key,
+                   uint64_t* i1, uint64_t* i2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DL_H */

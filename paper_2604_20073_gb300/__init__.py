@@ -1,0 +1,328 @@
+"""Python binding of libdlgpu.so, the GB300 semi-naive WCOJ Datalog library.
+
+The ``dl_*`` functions below carry the same names and arguments as the C ABI in
+``include/dl.h`` and only marshal arguments (ctypes).  Every step of the evaluation runs
+in the library's CUDA kernels; there is no Python or CPU fallback: if the library is
+missing or no GPU is present, creating an engine raises.
+
+PyTorch is used only as plumbing: the current CUDA stream (and, optionally, the caching
+allocator) is handed to the engine.  ``Engine`` wraps one engine handle with numpy-based
+convenience methods; ``run_program`` evaluates a whole program given as plain data:
+
+* ``relations``: ``{name: arity}``
+* ``facts``: ``{name: (rows, arity) uint32 array}``
+* ``rules``: list of ``(head, body, var_order)``; an atom is ``(relation, [terms])``, a term
+  is a ``str`` (variable) or an ``int`` (constant).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libdlgpu.so")
+
+DL_OK, DL_ERR_ARG, DL_ERR_UNSUPPORTED, DL_ERR_CAPACITY, DL_ERR_CUDA, DL_ERR_TIMEOUT, DL_ERR_STATE = range(7)
+ERR_NAMES = {1: "DL_ERR_ARG", 2: "DL_ERR_UNSUPPORTED", 3: "DL_ERR_CAPACITY", 4: "DL_ERR_CUDA",
+             5: "DL_ERR_TIMEOUT", 6: "DL_ERR_STATE"}
+DL_FLAG_NAIVE_ROOTS = 0x1
+DL_FLAG_DEBUG_CHECKS = 0x2
+DL_SINK_STORE, DL_SINK_COUNT = 0, 1
+DL_TERM_VAR, DL_TERM_CONST = 0, 1
+DL_MAX_STRATA = 64
+
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+DL_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p)
+DL_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class dl_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
+                ("alloc", DL_ALLOC_FN), ("free", DL_FREE_FN), ("alloc_user", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32), ("tile_units", ctypes.c_uint32)]
+
+
+class dl_term(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("id", ctypes.c_uint32)]
+
+
+class dl_atom(ctypes.Structure):
+    _fields_ = [("rel", ctypes.c_uint32), ("arity", ctypes.c_uint32), ("terms", ctypes.POINTER(dl_term))]
+
+
+class dl_stats(ctypes.Structure):
+    _fields_ = [("nstrata", ctypes.c_uint32), ("rounds", ctypes.c_uint32 * DL_MAX_STRATA),
+                ("stratum_first_rel", ctypes.c_uint32 * DL_MAX_STRATA), ("total_rounds", ctypes.c_uint32),
+                ("join_rows", ctypes.c_uint64), ("count_rows", ctypes.c_uint64), ("delta_rows", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("ms_total", ctypes.c_double), ("ms_join", ctypes.c_double), ("ms_sort", ctypes.c_double),
+                ("ms_dedup", ctypes.c_double), ("ms_merge", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/dl.h
+_SIGS = {
+    "dl_version": (ctypes.c_char_p, []),
+    "dl_engine_create": (ctypes.c_int, [ctypes.POINTER(dl_config), ctypes.POINTER(ctypes.c_void_p)]),
+    "dl_engine_destroy": (None, [ctypes.c_void_p]),
+    "dl_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "dl_relation_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_uint32, _u32p]),
+    "dl_relation_set_sink": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]),
+    "dl_load_facts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(_u32p), ctypes.c_uint64]),
+    "dl_load_facts_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u32p, ctypes.c_uint64]),
+    "dl_load_facts_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.c_uint64]),
+    "dl_relation_clear": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "dl_rule_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_atom), ctypes.POINTER(dl_atom),
+                                   ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p]),
+    "dl_fixpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_stats)]),
+    "dl_stratum_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p, _u32p]),
+    "dl_relation_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u64p]),
+    "dl_fetch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(_u32p), ctypes.c_uint64, _u64p]),
+    "dl_fetch_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.c_uint64, _u64p]),
+    "dl_fetch_digest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p]),
+    "dl_partition_slices": (ctypes.c_int, [_u64p, ctypes.c_uint64, ctypes.c_uint32, _u64p, _u64p]),
+    "dl_decode_unit": (ctypes.c_int, [_u64p, _u64p, ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p, _u64p]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdlgpu.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list:
+    return list(_SIGS)
+
+
+class DatalogError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def __getattr__(name):  # module-level dl_* access: paper_2604_20073_gb300.dl_fixpoint(...)
+    if name in _SIGS:
+        return getattr(load_library(), name)
+    raise AttributeError(name)
+
+
+def _cols_ptrs(arrs):
+    arr = (_u32p * len(arrs))()
+    for i, a in enumerate(arrs):
+        arr[i] = a.ctypes.data_as(_u32p)
+    return arr
+
+
+class Engine:
+    """One engine handle (owns all of its device memory)."""
+
+    def __init__(self, device: int = 0, stream=None, arena_bytes: int = 0, flags: int = 0, tile_units: int = 0,
+                 use_torch_allocator: bool = False):
+        import torch  # plumbing only: stream handle and (optionally) the caching allocator
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the Datalog engine runs only on the GPU")
+        torch.cuda.set_device(device)
+        cfg = dl_config()
+        cfg.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._torch_stream = stream
+        cfg.stream = ctypes.c_void_p(stream.cuda_stream)
+        cfg.arena_bytes = arena_bytes
+        cfg.flags = flags
+        cfg.tile_units = tile_units
+        self._cb = None
+        if use_torch_allocator:
+            def _alloc(nbytes, strm, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, strm)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, strm, user):
+                torch.cuda.caching_allocator_delete(ptr)
+            self._cb = (DL_ALLOC_FN(_alloc), DL_FREE_FN(_free))
+            cfg.alloc, cfg.free = self._cb
+        h = ctypes.c_void_p()
+        rc = self.lib.dl_engine_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != DL_OK:
+            raise DatalogError(rc, "dl_engine_create failed")
+        self.h = h
+        self.rel_ids: dict = {}
+        self.arity: dict = {}
+        self.names: list = []
+
+    def _check(self, rc):
+        if rc != DL_OK:
+            raise DatalogError(rc, self.lib.dl_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dl_engine_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def relation(self, name: str, arity: int) -> int:
+        rid = ctypes.c_uint32()
+        self._check(self.lib.dl_relation_create(self.h, name.encode(), arity, ctypes.byref(rid)))
+        self.rel_ids[name] = rid.value
+        self.arity[name] = arity
+        self.names.append(name)
+        return rid.value
+
+    def set_sink(self, name: str, sink: int):
+        self._check(self.lib.dl_relation_set_sink(self.h, self.rel_ids[name], sink))
+
+    def load(self, name: str, rows):
+        """rows: (n, arity) uint32 numpy array on the host, or a torch CUDA tensor of shape (arity, n)."""
+        if hasattr(rows, "is_cuda") and rows.is_cuda:
+            cols = [rows[c].contiguous() for c in range(rows.shape[0])]
+            ptrs = (ctypes.c_void_p * len(cols))(*[c.data_ptr() for c in cols])
+            self._check(self.lib.dl_load_facts_device(self.h, self.rel_ids[name], ptrs, cols[0].numel()))
+            return
+        rows = np.asarray(rows, dtype=np.uint32).reshape(-1, self.arity[name])
+        cols = [np.ascontiguousarray(rows[:, c]) for c in range(rows.shape[1])]
+        self._check(self.lib.dl_load_facts(self.h, self.rel_ids[name], _cols_ptrs(cols), rows.shape[0]))
+
+    def clear(self, name: str):
+        self._check(self.lib.dl_relation_clear(self.h, self.rel_ids[name]))
+
+    def _atom(self, atom, var_ids, keep):
+        rel, terms = atom
+        ts = (dl_term * len(terms))()
+        for i, t in enumerate(terms):
+            if isinstance(t, str):
+                ts[i].kind, ts[i].id = DL_TERM_VAR, var_ids.setdefault(t, len(var_ids))
+            else:
+                ts[i].kind, ts[i].id = DL_TERM_CONST, int(t)
+        keep.append(ts)
+        a = dl_atom()
+        a.rel, a.arity, a.terms = self.rel_ids[rel], len(terms), ts
+        return a
+
+    def rule(self, head, body, order):
+        var_ids: dict = {}
+        keep: list = []
+        batoms = (dl_atom * len(body))()
+        for i, b in enumerate(body):
+            batoms[i] = self._atom(b, var_ids, keep)
+        h = self._atom(head, var_ids, keep)
+        ordr = (ctypes.c_uint32 * len(order))(*[var_ids.get(v, 1023) for v in order])
+        rid = ctypes.c_uint32()
+        self._check(self.lib.dl_rule_add(self.h, ctypes.byref(h), batoms, len(body), ordr, len(order),
+                                         ctypes.byref(rid)))
+        return rid.value
+
+    def fixpoint(self) -> dict:
+        st = dl_stats()
+        self._check(self.lib.dl_fixpoint(self.h, ctypes.byref(st)))
+        out = {f: getattr(st, f) for f, _ in dl_stats._fields_ if f not in ("rounds", "stratum_first_rel")}
+        out["rounds"] = list(st.rounds[: min(st.nstrata, DL_MAX_STRATA)])
+        return out
+
+    def strata(self) -> list:
+        out = []
+        s = 0
+        while True:
+            rels = (ctypes.c_uint32 * 256)()
+            n = ctypes.c_uint32()
+            r = ctypes.c_uint32()
+            rc = self.lib.dl_stratum_info(self.h, s, rels, 256, ctypes.byref(n), ctypes.byref(r))
+            if rc != DL_OK:
+                break
+            out.append((sorted(self.names[i] for i in rels[: n.value]), r.value))
+            s += 1
+        return out
+
+    def size(self, name: str) -> int:
+        n = ctypes.c_uint64()
+        self._check(self.lib.dl_relation_size(self.h, self.rel_ids[name], ctypes.byref(n)))
+        return n.value
+
+    def fetch(self, name: str) -> np.ndarray:
+        n = ctypes.c_uint64()
+        rid = self.rel_ids[name]
+        self._check(self.lib.dl_fetch(self.h, rid, None, 0, ctypes.byref(n)))
+        a = self.arity[name]
+        cols = [np.empty(n.value, dtype=np.uint32) for _ in range(a)]
+        self._check(self.lib.dl_fetch(self.h, rid, _cols_ptrs(cols), n.value, ctypes.byref(n)))
+        return np.stack(cols, axis=1) if a else np.zeros((0, 0), np.uint32)
+
+    def fetch_into(self, name: str, cols: list) -> int:
+        """Fetch into caller-provided host column buffers (e.g. pinned); returns the row count."""
+        n = ctypes.c_uint64()
+        cap = min(c.size for c in cols)
+        self._check(self.lib.dl_fetch(self.h, self.rel_ids[name], _cols_ptrs(cols), cap, ctypes.byref(n)))
+        return n.value
+
+    def fetch_device(self, name: str, cols: list) -> int:
+        """Fetch into torch CUDA tensors (one per column); returns the row count."""
+        n = ctypes.c_uint64()
+        ptrs = (ctypes.c_void_p * len(cols))(*[c.data_ptr() for c in cols])
+        cap = min(c.numel() for c in cols)
+        self._check(self.lib.dl_fetch_device(self.h, self.rel_ids[name], ptrs, cap, ctypes.byref(n)))
+        return n.value
+
+    def digest(self, name: str) -> tuple:
+        c = ctypes.c_uint64()
+        d = (ctypes.c_uint64 * 2)()
+        self._check(self.lib.dl_fetch_digest(self.h, self.rel_ids[name], ctypes.byref(c), d))
+        return (c.value, d[0], d[1])
+
+
+def build_program(eng: Engine, relations: dict, rules: list, sinks: dict | None = None):
+    for name, a in relations.items():
+        eng.relation(name, a)
+    for name, s in (sinks or {}).items():
+        eng.set_sink(name, s)
+    for r in rules:
+        eng.rule(r[0], r[1], r[2])
+
+
+def run_program(relations: dict, facts: dict, rules: list, sinks: dict | None = None, **cfg):
+    """Evaluate a program on the GPU; returns (relations dict, strata list, stats dict)."""
+    with Engine(**cfg) as eng:
+        build_program(eng, relations, rules, sinks)
+        for name, rows in facts.items():
+            eng.load(name, rows)
+        stats = eng.fixpoint()
+        out = {}
+        for name in relations:
+            if (sinks or {}).get(name, DL_SINK_STORE) == DL_SINK_COUNT:
+                out[name] = eng.digest(name)
+            else:
+                out[name] = eng.fetch(name)
+        return out, eng.strata(), stats

@@ -1,0 +1,930 @@
+// C ABI entry points and the host runtime: relation store, stratification, semi-naive
+// rounds (paper Sections 2 and 4), fetch.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <set>
+
+#include "engine.h"
+
+namespace dl {
+
+Perm atom_perm(const Rule& R, uint32_t a);
+bool head_is_order(const Rule& R);
+
+// ------------------------------------------------------------------ memory
+
+DevMem::DevMem(Engine* e, size_t b) : eng(e), bytes(b) { ptr = e->alloc(b); }
+DevMem::~DevMem() {
+    if (ptr) eng->release(ptr, bytes);
+}
+
+namespace {
+std::map<Engine*, cudaMemPool_t> g_pools;  // engine-owned stream-ordered pools
+}
+
+void* Engine::alloc(size_t bytes) {
+    if (bytes == 0) bytes = 1;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (used + bytes > budget)
+        throw Error(DL_ERR_CAPACITY, "device budget exceeded: need " + std::to_string(bytes) + " more bytes, " +
+                                         std::to_string(used) + " of " + std::to_string(budget) + " in use");
+    void* p = nullptr;
+    if (ualloc) {
+        p = ualloc(bytes, stream, uuser);
+        if (!p) throw Error(DL_ERR_CAPACITY, "user allocator returned NULL");
+    } else {
+        cudaError_t st = cudaMallocFromPoolAsync(&p, bytes, g_pools[this], stream);
+        if (st == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            throw Error(DL_ERR_CAPACITY, "device out of memory");
+        }
+        if (st != cudaSuccess) throw Error(DL_ERR_CUDA, std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(st));
+    }
+    used += bytes;
+    peak = std::max(peak, used);
+    return p;
+}
+
+void Engine::release(void* p, size_t bytes) {
+    if (bytes == 0) bytes = 1;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (ufree) ufree(p, bytes, stream, uuser);
+    else cudaFreeAsync(p, stream);
+    used -= bytes;
+}
+
+const uint64_t* Engine::readback(const void* dev, size_t words) {
+    if (words > 64) throw Error(DL_ERR_ARG, "readback too large");
+    DL_CUDA(cudaMemcpyAsync(host_scratch, dev, words * 8, cudaMemcpyDeviceToHost, stream));
+    DL_CUDA(cudaStreamSynchronize(stream));
+    return host_scratch;
+}
+
+cudaEvent_t Engine::next_event() {
+    if (event_next == event_pool.size()) {
+        cudaEvent_t ev;
+        DL_CUDA(cudaEventCreate(&ev));
+        event_pool.push_back(ev);
+    }
+    return event_pool[event_next++];
+}
+
+void Engine::phase_begin(int kind) {
+    cudaEvent_t a = next_event();
+    DL_CUDA(cudaEventRecord(a, stream));
+    phases.ev[kind].push_back({a, nullptr});
+}
+
+void Engine::phase_end(int kind) {
+    cudaEvent_t b = next_event();
+    DL_CUDA(cudaEventRecord(b, stream));
+    phases.ev[kind].back().second = b;
+}
+
+Engine::~Engine() {
+    rels.clear();
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto ev : event_pool) cudaEventDestroy(ev);
+    if (host_scratch) cudaFreeHost(host_scratch);
+    auto it = g_pools.find(this);
+    if (it != g_pools.end()) {
+        cudaMemPoolDestroy(it->second);
+        g_pools.erase(it);
+    }
+    if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+// ------------------------------------------------------------------ indexes
+
+Index make_index(Engine& E, uint32_t arity, const Perm& perm, uint64_t n) {
+    Index ix;
+    ix.arity = arity;
+    for (int k = 0; k < kMaxArity; k++) ix.perm[k] = perm[k];
+    ix.n = n;
+    ix.cap = std::max<uint64_t>(n, 1);
+    ix.cols = E.make(sizeof(uint32_t) * arity * ix.cap);
+    return ix;
+}
+
+TableView table_of(const Index& ix) {
+    TableView t;
+    memset(&t, 0, sizeof(t));
+    t.arity = ix.arity;
+    t.n = ix.n;
+    for (uint32_t k = 0; k < ix.arity; k++) t.col[k] = ix.col((int)k);
+    return t;
+}
+
+AtomView atom_of(const Index& ix) {
+    AtomView a;
+    memset(&a, 0, sizeof(a));
+    for (uint32_t k = 0; k < ix.arity; k++) a.col[k] = ix.col((int)k);
+    a.root = ix.root_ptr();
+    a.V = ix.rootV;
+    a.n = (uint32_t)ix.n;
+    a.arity = ix.arity;
+    return a;
+}
+
+namespace {
+
+const char* kVersion = "1.0.0";
+
+bool same_perm(const Perm& a, const Perm& b, uint32_t arity) {
+    for (uint32_t k = 0; k < arity; k++)
+        if (a[k] != b[k]) return false;
+    return true;
+}
+
+Index empty_index(uint32_t arity, const Perm& perm) {
+    Index ix;
+    ix.arity = arity;
+    for (int k = 0; k < kMaxArity; k++) ix.perm[k] = perm[k];
+    return ix;
+}
+
+// Sort a table (canonical column order of its index) in place; returns an Index holding it.
+// `buf` owns t's columns; the result owns whichever buffer ends up holding the sorted rows.
+Index sort_into_index(Engine& E, DevPtr buf, TableView t, const Perm& perm, uint32_t arity) {
+    Index ix = empty_index(arity, perm);
+    ix.n = t.n;
+    ix.cap = std::max<uint64_t>(t.n, 1);
+    if (t.n <= 1) {
+        ix.cols = buf;
+        return ix;
+    }
+    DevPtr tmpbuf = E.make(sizeof(uint32_t) * arity * ix.cap);
+    TableView tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.arity = arity;
+    tmp.n = t.n;
+    for (uint32_t c = 0; c < arity; c++) tmp.col[c] = (uint32_t*)tmpbuf->ptr + (size_t)c * ix.cap;
+    uint32_t* orig0 = t.col[0];
+    E.phase_begin(1);
+    radix_sort_rows(E, t, tmp, nullptr);
+    E.phase_end(1);
+    ix.cols = (t.col[0] == orig0) ? buf : tmpbuf;
+    return ix;
+}
+
+void build_roots(Engine& E, Index& ix, bool needed) {
+    ix.root.reset();
+    ix.rootV = 0;
+    if (!needed || E.V == 0 || E.V > kDenseRootLimit || ix.n == 0) return;
+    ix.root = E.make(sizeof(uint32_t) * ((size_t)E.V + 1));
+    ix.rootV = E.V;
+    build_root(E, ix.col(0), ix.n, (uint32_t*)ix.root->ptr, E.V);
+}
+
+// Δ = unique(sorted new rows) \ full, written into a fresh index (canonical order).
+Index compute_delta(Engine& E, const Index& sorted_new, const Index& full, const Perm& perm, uint32_t arity,
+                    bool known_unique) {
+    if (sorted_new.n == 0) return empty_index(arity, perm);
+    if (full.n == 0 && known_unique) return sorted_new;
+    Index d = make_index(E, arity, perm, sorted_new.n);
+    AtomView fa = atom_of(full);
+    E.phase_begin(2);
+    d.n = unique_anti(E, table_of(sorted_new), full.n ? &fa : nullptr, table_of(d));
+    E.phase_end(2);
+    return d;
+}
+
+Index merge_into(Engine& E, const Index& full, const Index& delta) {
+    if (delta.n == 0) return full;
+    if (full.n == 0) return delta;
+    if (full.n + delta.n >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "relation index of 2^32 rows or more");
+    Index out = make_index(E, full.arity, [&] {
+        Perm p;
+        for (int k = 0; k < kMaxArity; k++) p[k] = full.perm[k];
+        return p;
+    }(), full.n + delta.n);
+    E.phase_begin(3);
+    merge_rows(E, table_of(full), table_of(delta), table_of(out));
+    E.phase_end(3);
+    return out;
+}
+
+Index permuted_sorted(Engine& E, const Index& canon, const Perm& perm) {
+    const uint32_t a = canon.arity;
+    Index ix = empty_index(a, perm);
+    if (canon.n == 0) return ix;
+    DevPtr buf = E.make(sizeof(uint32_t) * a * canon.n);
+    TableView t;
+    memset(&t, 0, sizeof(t));
+    t.arity = a;
+    t.n = canon.n;
+    for (uint32_t c = 0; c < a; c++) t.col[c] = (uint32_t*)buf->ptr + (size_t)c * canon.n;
+    permute_copy(E, table_of(canon), perm.data(), t);
+    return sort_into_index(E, buf, t, perm, a);
+}
+
+void check_sorted(Engine& E, const Index& ix, const std::string& what) {
+    if (!(E.flags & DL_FLAG_DEBUG_CHECKS)) return;
+    uint64_t bad = count_order_violations(E, table_of(ix));
+    if (bad) throw Error(DL_ERR_STATE, "debug check: " + what + " has " + std::to_string(bad) + " order violations");
+}
+
+// Add rows (canonical column order, any order, duplicates allowed) to a relation's full index.
+void add_rows(Engine& E, Relation& R, DevPtr buf, TableView t) {
+    if (t.n == 0) return;
+    Index sorted = sort_into_index(E, buf, t, identity_perm(), R.arity);
+    Index d = compute_delta(E, sorted, R.full[0], identity_perm(), R.arity, false);
+    R.full[0] = merge_into(E, R.full[0], d);
+    R.full_perms_built = false;
+    check_sorted(E, R.full[0], R.name);
+}
+
+void update_max_value(Engine& E, const TableView& t) {
+    if (!t.n) return;
+    auto m = E.array<uint32_t>(2);
+    DL_CUDA(cudaMemsetAsync(m.p, 0, 8, E.stream));
+    for (uint32_t c = 0; c < t.arity; c++) column_max(E, t.col[c], t.n, m.p);
+    uint32_t mx = (uint32_t)(E.readback(m.p, 1)[0] & 0xffffffffu);
+    if (mx == 0xffffffffu) throw Error(DL_ERR_UNSUPPORTED, "value 0xFFFFFFFF is reserved");
+    E.V = std::max(E.V, mx + 1);
+}
+
+uint32_t perm_slot(Relation& R, const Perm& p) {
+    for (size_t k = 0; k < R.perms.size(); k++)
+        if (same_perm(R.perms[k], p, R.arity)) return (uint32_t)k;
+    R.perms.push_back(p);
+    R.full.push_back(empty_index(R.arity, p));
+    R.delta.push_back(empty_index(R.arity, p));
+    R.root_needed.push_back(false);
+    R.full_perms_built = false;
+    return (uint32_t)(R.perms.size() - 1);
+}
+
+void ensure_full_perms(Engine& E, Relation& R) {
+    if (!R.full_perms_built) {
+        for (size_t k = 1; k < R.perms.size(); k++) R.full[k] = permuted_sorted(E, R.full[0], R.perms[k]);
+        R.full_perms_built = true;
+    }
+    for (size_t k = 0; k < R.perms.size(); k++) build_roots(E, R.full[k], R.root_needed[k]);
+}
+
+// ------------------------------------------------------------------ strata
+
+// Kosaraju's SCC over relations (edge: body relation -> head relation); components in
+// topological order, ties broken by the smallest relation id.
+std::vector<Stratum> stratify(const Engine& E) {
+    const uint32_t n = (uint32_t)E.rels.size();
+    std::vector<std::vector<uint32_t>> g(n), gr(n);
+    std::vector<bool> derived(n, false);
+    for (const Rule& r : E.rules) {
+        derived[r.head.rel] = true;
+        for (const RuleAtom& a : r.body) {
+            g[a.rel].push_back(r.head.rel);
+            gr[r.head.rel].push_back(a.rel);
+        }
+    }
+    std::vector<uint32_t> finish;
+    std::vector<bool> seen(n, false);
+    for (uint32_t s = 0; s < n; s++) {
+        if (seen[s]) continue;
+        std::vector<std::pair<uint32_t, size_t>> st{{s, 0}};
+        seen[s] = true;
+        while (!st.empty()) {
+            auto& [v, i] = st.back();
+            if (i < g[v].size()) {
+                uint32_t w = g[v][i++];
+                if (!seen[w]) {
+                    seen[w] = true;
+                    st.push_back({w, 0});
+                }
+            } else {
+                finish.push_back(v);
+                st.pop_back();
+            }
+        }
+    }
+    std::vector<int> comp(n, -1);
+    int nc = 0;
+    for (auto it = finish.rbegin(); it != finish.rend(); ++it) {
+        if (comp[*it] >= 0) continue;
+        std::vector<uint32_t> st{*it};
+        comp[*it] = nc;
+        while (!st.empty()) {
+            uint32_t v = st.back();
+            st.pop_back();
+            for (uint32_t w : gr[v])
+                if (comp[w] < 0) {
+                    comp[w] = nc;
+                    st.push_back(w);
+                }
+        }
+        nc++;
+    }
+    std::vector<std::set<int>> succ(nc);
+    std::vector<int> indeg(nc, 0), minrel(nc, INT32_MAX);
+    for (uint32_t v = 0; v < n; v++) minrel[comp[v]] = std::min(minrel[comp[v]], (int)v);
+    for (uint32_t v = 0; v < n; v++)
+        for (uint32_t w : g[v])
+            if (comp[v] != comp[w] && succ[comp[v]].insert(comp[w]).second) indeg[comp[w]]++;
+    std::set<std::pair<int, int>> ready;  // (min relation id, component)
+    for (int c = 0; c < nc; c++)
+        if (!indeg[c]) ready.insert({minrel[c], c});
+    std::vector<Stratum> out;
+    while (!ready.empty()) {
+        int c = ready.begin()->second;
+        ready.erase(ready.begin());
+        Stratum s;
+        bool has_rule = false;
+        for (uint32_t v = 0; v < n; v++)
+            if (comp[v] == c) {
+                s.rels.push_back(v);
+                has_rule = has_rule || derived[v];
+            }
+        if (has_rule) out.push_back(s);
+        for (int w : succ[c])
+            if (--indeg[w] == 0) ready.insert({minrel[w], w});
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------ rounds
+
+struct Variant {
+    const Rule* rule;
+    int delta_atom;   // -1: all atoms read full
+};
+
+struct PendingOut {
+    JoinOutput out;
+    uint32_t producers = 0;   // variants that produced parts
+};
+
+// Turn one round's join outputs for relation R into its new delta; merge into full.
+// Returns |Δ|.
+uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
+    JoinOutput& jo = P.out;
+    Index newrows = empty_index(R.arity, identity_perm());
+    bool known_unique = false;
+    if (jo.parts.size() == 1 && jo.sorted_unique) {
+        newrows.n = jo.parts[0].n;
+        newrows.cap = newrows.n;
+        newrows.cols = jo.owners[0];
+        known_unique = true;
+    } else if (!jo.parts.empty()) {
+        uint64_t tot = 0;
+        for (auto& p : jo.parts) tot += p.n;
+        if (tot >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "round output of 2^32 rows or more");
+        DevPtr buf = E.make(sizeof(uint32_t) * R.arity * tot);
+        TableView t;
+        memset(&t, 0, sizeof(t));
+        t.arity = R.arity;
+        t.n = tot;
+        for (uint32_t c = 0; c < R.arity; c++) t.col[c] = (uint32_t*)buf->ptr + (size_t)c * tot;
+        uint64_t off = 0;
+        for (auto& p : jo.parts) {
+            for (uint32_t c = 0; c < R.arity; c++)
+                DL_CUDA(cudaMemcpyAsync(t.col[c] + off, p.col[c], sizeof(uint32_t) * p.n, cudaMemcpyDeviceToDevice,
+                                        E.stream));
+            off += p.n;
+        }
+        jo.parts.clear();
+        jo.owners.clear();
+        newrows = sort_into_index(E, buf, t, identity_perm(), R.arity);
+    }
+    Index d = compute_delta(E, newrows, R.full[0], identity_perm(), R.arity, known_unique);
+    jo.parts.clear();
+    jo.owners.clear();
+    E.delta_rows += d.n;
+    if (keep_delta) {
+        for (size_t k = 0; k < R.perms.size(); k++) R.delta[k] = empty_index(R.arity, R.perms[k]);
+        R.delta[0] = d;
+    }
+    if (d.n == 0) return 0;
+    R.full[0] = merge_into(E, R.full[0], d);
+    check_sorted(E, R.full[0], R.name);
+    build_roots(E, R.full[0], R.root_needed[0]);
+    for (size_t k = 1; k < R.perms.size(); k++) {
+        Index dk = permuted_sorted(E, d, R.perms[k]);
+        R.full[k] = merge_into(E, R.full[k], dk);
+        build_roots(E, R.full[k], R.root_needed[k]);
+        if (keep_delta) {
+            build_roots(E, dk, R.root_needed[k]);
+            R.delta[k] = dk;
+        }
+    }
+    if (keep_delta) {
+        Index d0 = d;
+        build_roots(E, d0, R.root_needed[0]);
+        R.delta[0] = d0;
+    }
+    R.full_perms_built = true;
+    return d.n;
+}
+
+void run_variant(Engine& E, const Variant& v, std::map<uint32_t, PendingOut>& outs) {
+    const Rule& r = *v.rule;
+    std::vector<const Index*> src(r.body.size());
+    for (size_t a = 0; a < r.body.size(); a++) {
+        Relation& B = E.rels[r.body[a].rel];
+        uint32_t slot = perm_slot(B, atom_perm(r, (uint32_t)a));
+        src[a] = (int)a == v.delta_atom ? &B.delta[slot] : &B.full[slot];
+    }
+    Relation& H = E.rels[r.head.rel];
+    PendingOut& po = outs[r.head.rel];
+    JoinOutput jo;
+    run_join(E, r, src, H, jo);
+    if (!jo.parts.empty()) {
+        po.producers++;
+        po.out.sorted_unique = (po.producers == 1) && jo.sorted_unique;
+        for (size_t i = 0; i < jo.parts.size(); i++) {
+            po.out.parts.push_back(jo.parts[i]);
+            po.out.owners.push_back(jo.owners[i]);
+        }
+        if (jo.parts.size() > 1) po.out.sorted_unique = false;
+    }
+}
+
+void validate_program(Engine& E) {
+    for (size_t ri = 0; ri < E.rules.size(); ri++) {
+        const Rule& r = E.rules[ri];
+        for (const RuleAtom& a : r.body)
+            if (E.rels[a.rel].sink == DL_SINK_COUNT)
+                throw Error(DL_ERR_UNSUPPORTED, "count sink '" + E.rels[a.rel].name + "' used in a rule body");
+        if (E.rels[r.head.rel].sink == DL_SINK_COUNT) {
+            int n = 0;
+            for (const Rule& q : E.rules) n += q.head.rel == r.head.rel;
+            std::set<uint32_t> hv;
+            bool ok = n == 1 && r.head.arity == r.order.size();
+            for (uint32_t c = 0; c < r.head.arity && ok; c++)
+                ok = r.head.terms[c].kind == DL_TERM_VAR && hv.insert(r.head.terms[c].id).second;
+            if (!ok)
+                throw Error(DL_ERR_UNSUPPORTED, "count sink '" + E.rels[r.head.rel].name +
+                                                    "' needs exactly one rule whose head lists each body variable once");
+        }
+    }
+}
+
+void fixpoint(Engine& E, dl_stats* st) {
+    auto t0 = std::chrono::steady_clock::now();
+    const uint64_t launches0 = E.launches;
+    E.join_rows = E.count_rows = E.delta_rows = 0;
+    E.peak = E.used;
+    E.event_next = 0;
+    for (auto& v : E.phases.ev) v.clear();
+    validate_program(E);
+    // plan: index permutations each atom reads; roots for every index a join probes
+    for (const Rule& r : E.rules)
+        for (uint32_t a = 0; a < r.body.size(); a++) {
+            Relation& B = E.rels[r.body[a].rel];
+            uint32_t slot = perm_slot(B, atom_perm(r, a));
+            B.root_needed[slot] = true;
+        }
+    for (Relation& R : E.rels) {
+        if (R.sink == DL_SINK_COUNT) {
+            R.sink_count = 0;
+            R.sink_digest[0] = R.sink_digest[1] = 0;
+            continue;
+        }
+        ensure_full_perms(E, R);
+    }
+    E.strata = stratify(E);
+    for (auto& R : E.rels) R.stratum = -1;
+    for (size_t s = 0; s < E.strata.size(); s++)
+        for (uint32_t r : E.strata[s].rels) E.rels[r].stratum = (int)s;
+
+    for (size_t s = 0; s < E.strata.size(); s++) {
+        Stratum& S = E.strata[s];
+        std::vector<Variant> round1, rec;
+        for (const Rule& r : E.rules) {
+            if (E.rels[r.head.rel].stratum != (int)s) continue;
+            bool is_rec = false;
+            for (const RuleAtom& a : r.body) is_rec = is_rec || E.rels[a.rel].stratum == (int)s;
+            if (!is_rec) {
+                round1.push_back({&r, -1});
+            } else {
+                for (size_t j = 0; j < r.body.size(); j++)
+                    if (E.rels[r.body[j].rel].stratum == (int)s) rec.push_back({&r, (int)j});
+            }
+        }
+        // Round 1: non-recursive rules over full relations; Δ1 = everything now in the stratum.
+        std::map<uint32_t, PendingOut> outs;
+        for (const Variant& v : round1) run_variant(E, v, outs);
+        bool any = false;
+        for (uint32_t r : S.rels) {
+            Relation& R = E.rels[r];
+            if (R.sink == DL_SINK_COUNT) continue;
+            absorb_round(E, R, outs[r], false);
+            if (!rec.empty()) {
+                for (size_t k = 0; k < R.perms.size(); k++) R.delta[k] = R.full[k];
+                any = any || R.full[0].n > 0;
+            }
+        }
+        uint32_t t = 1;
+        if (!rec.empty() && any) {
+            for (;;) {
+                t++;
+                outs.clear();
+                for (const Variant& v : rec) run_variant(E, v, outs);
+                uint64_t nd = 0;
+                for (uint32_t r : S.rels) {
+                    Relation& R = E.rels[r];
+                    if (R.sink == DL_SINK_COUNT) continue;
+                    nd += absorb_round(E, R, outs[r], true);
+                }
+                if (nd == 0) break;
+            }
+        }
+        S.rounds = t;
+        for (uint32_t r : S.rels) {
+            Relation& R = E.rels[r];
+            for (size_t k = 0; k < R.delta.size(); k++) R.delta[k] = empty_index(R.arity, R.perms[k]);
+        }
+    }
+    E.sync();
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->nstrata = (uint32_t)E.strata.size();
+        for (size_t s = 0; s < E.strata.size(); s++) {
+            st->total_rounds += E.strata[s].rounds;
+            if (s < DL_MAX_STRATA) {
+                st->rounds[s] = E.strata[s].rounds;
+                st->stratum_first_rel[s] = E.strata[s].rels.front();
+            }
+        }
+        st->join_rows = E.join_rows;
+        st->count_rows = E.count_rows;
+        st->delta_rows = E.delta_rows;
+        st->peak_bytes = E.peak;
+        st->kernel_launches = E.launches - launches0;
+        double* ms[4] = {&st->ms_join, &st->ms_sort, &st->ms_dedup, &st->ms_merge};
+        for (int k = 0; k < 4; k++)
+            for (auto& pr : E.phases.ev[k]) {
+                float f = 0;
+                if (pr.second && cudaEventElapsedTime(&f, pr.first, pr.second) == cudaSuccess) *ms[k] += f;
+            }
+        st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+}
+
+int guard(dl_engine* h, const std::function<void(Engine&)>& fn) {
+    if (!h) return DL_ERR_ARG;
+    Engine& E = *reinterpret_cast<Engine*>(h);
+    E.err.clear();
+    try {
+        DL_CUDA(cudaSetDevice(E.device));
+        fn(E);
+        return DL_OK;
+    } catch (const Error& x) {
+        E.err = x.what();
+        return x.code;
+    } catch (const std::bad_alloc&) {
+        E.err = "host out of memory";
+        return DL_ERR_CAPACITY;
+    } catch (const std::exception& x) {
+        E.err = x.what();
+        return DL_ERR_CUDA;
+    }
+}
+
+Relation& rel_of(Engine& E, dl_rel_id r) {
+    if (r >= E.rels.size()) throw Error(DL_ERR_ARG, "bad relation id " + std::to_string(r));
+    return E.rels[r];
+}
+
+void load_table(Engine& E, Relation& R, DevPtr buf, TableView t) {
+    if (R.sink == DL_SINK_COUNT) throw Error(DL_ERR_STATE, "cannot load facts into a count sink");
+    update_max_value(E, t);
+    add_rows(E, R, buf, t);
+}
+
+}  // namespace
+}  // namespace dl
+
+using namespace dl;
+
+extern "C" {
+
+const char* dl_version(void) { return kVersion; }
+
+int dl_engine_create(const dl_config* cfg, dl_engine** out) {
+    if (!out) return DL_ERR_ARG;
+    *out = nullptr;
+    dl_config c;
+    memset(&c, 0, sizeof(c));
+    c.device = -1;
+    if (cfg) c = *cfg;
+    if ((c.alloc == nullptr) != (c.free == nullptr)) return DL_ERR_ARG;
+    Engine* E = new (std::nothrow) Engine();
+    if (!E) return DL_ERR_CAPACITY;
+    try {
+        if (c.device < 0) DL_CUDA(cudaGetDevice(&E->device));
+        else E->device = c.device;
+        DL_CUDA(cudaSetDevice(E->device));
+        if (c.stream) {
+            E->stream = (cudaStream_t)c.stream;
+        } else {
+            DL_CUDA(cudaStreamCreateWithFlags(&E->stream, cudaStreamNonBlocking));
+            E->own_stream = true;
+        }
+        size_t fr = 0, tot = 0;
+        DL_CUDA(cudaMemGetInfo(&fr, &tot));
+        E->budget = c.arena_bytes ? c.arena_bytes : (uint64_t)(fr * 0.9);
+        E->ualloc = c.alloc;
+        E->ufree = c.free;
+        E->uuser = c.alloc_user;
+        E->flags = c.flags;
+        E->tile_units = c.tile_units ? c.tile_units : 4096;
+        DL_CUDA(cudaMallocHost(&E->host_scratch, 64 * sizeof(uint64_t)));
+        if (!E->ualloc) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = E->device;
+            cudaMemPool_t pool;
+            DL_CUDA(cudaMemPoolCreate(&pool, &props));
+            uint64_t thr = UINT64_MAX;
+            DL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+            g_pools[E] = pool;
+        }
+    } catch (const Error& x) {
+        int code = x.code;
+        delete E;
+        return code;
+    }
+    *out = reinterpret_cast<dl_engine*>(E);
+    return DL_OK;
+}
+
+void dl_engine_destroy(dl_engine* e) {
+    if (!e) return;
+    Engine* E = reinterpret_cast<Engine*>(e);
+    cudaSetDevice(E->device);
+    delete E;
+}
+
+const char* dl_last_error(const dl_engine* e) {
+    if (!e) return "null engine";
+    return reinterpret_cast<const Engine*>(e)->err.c_str();
+}
+
+int dl_relation_create(dl_engine* e, const char* name, uint32_t arity, dl_rel_id* out) {
+    return guard(e, [&](Engine& E) {
+        if (!name || !*name) throw Error(DL_ERR_ARG, "empty relation name");
+        if (arity < 1 || arity > DL_MAX_ARITY) throw Error(DL_ERR_ARG, "arity out of range");
+        for (auto& r : E.rels)
+            if (r.name == name) throw Error(DL_ERR_ARG, std::string("duplicate relation name ") + name);
+        Relation R;
+        R.name = name;
+        R.arity = arity;
+        R.perms.push_back(identity_perm());
+        R.full.push_back(empty_index(arity, identity_perm()));
+        R.delta.push_back(empty_index(arity, identity_perm()));
+        R.root_needed.push_back(false);
+        E.rels.push_back(std::move(R));
+        if (out) *out = (dl_rel_id)(E.rels.size() - 1);
+    });
+}
+
+int dl_relation_set_sink(dl_engine* e, dl_rel_id rel, uint32_t sink) {
+    return guard(e, [&](Engine& E) {
+        Relation& R = rel_of(E, rel);
+        if (sink != DL_SINK_STORE && sink != DL_SINK_COUNT) throw Error(DL_ERR_ARG, "bad sink");
+        if (sink == DL_SINK_COUNT && R.full[0].n) throw Error(DL_ERR_STATE, "relation already holds tuples");
+        R.sink = sink;
+    });
+}
+
+int dl_load_facts(dl_engine* e, dl_rel_id rel, const uint32_t* const* cols, uint64_t nrows) {
+    return guard(e, [&](Engine& E) {
+        Relation& R = rel_of(E, rel);
+        if (nrows == 0) return;
+        if (!cols) throw Error(DL_ERR_ARG, "null column array");
+        for (uint32_t c = 0; c < R.arity; c++)
+            if (!cols[c]) throw Error(DL_ERR_ARG, "null column pointer");
+        if (nrows >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "2^32 rows or more in one load");
+        DevPtr buf = E.make(sizeof(uint32_t) * R.arity * nrows);
+        TableView t;
+        memset(&t, 0, sizeof(t));
+        t.arity = R.arity;
+        t.n = nrows;
+        for (uint32_t c = 0; c < R.arity; c++) {
+            t.col[c] = (uint32_t*)buf->ptr + (size_t)c * nrows;
+            DL_CUDA(cudaMemcpyAsync(t.col[c], cols[c], sizeof(uint32_t) * nrows, cudaMemcpyHostToDevice, E.stream));
+        }
+        load_table(E, R, buf, t);
+    });
+}
+
+int dl_load_facts_rows(dl_engine* e, dl_rel_id rel, const uint32_t* rows, uint64_t nrows) {
+    if (!e) return DL_ERR_ARG;
+    Engine& E = *reinterpret_cast<Engine*>(e);
+    if (rel >= E.rels.size()) {
+        E.err = "bad relation id";
+        return DL_ERR_ARG;
+    }
+    if (nrows == 0) return DL_OK;
+    if (!rows) {
+        E.err = "null rows";
+        return DL_ERR_ARG;
+    }
+    const uint32_t a = E.rels[rel].arity;
+    std::vector<std::vector<uint32_t>> cols(a, std::vector<uint32_t>(nrows));
+    for (uint64_t i = 0; i < nrows; i++)
+        for (uint32_t c = 0; c < a; c++) cols[c][i] = rows[i * a + c];
+    std::vector<const uint32_t*> ptrs(a);
+    for (uint32_t c = 0; c < a; c++) ptrs[c] = cols[c].data();
+    return dl_load_facts(e, rel, ptrs.data(), nrows);
+}
+
+int dl_load_facts_device(dl_engine* e, dl_rel_id rel, const uint32_t* const* dcols, uint64_t nrows) {
+    return guard(e, [&](Engine& E) {
+        Relation& R = rel_of(E, rel);
+        if (nrows == 0) return;
+        if (!dcols) throw Error(DL_ERR_ARG, "null column array");
+        if (nrows >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "2^32 rows or more in one load");
+        DevPtr buf = E.make(sizeof(uint32_t) * R.arity * nrows);
+        TableView t;
+        memset(&t, 0, sizeof(t));
+        t.arity = R.arity;
+        t.n = nrows;
+        for (uint32_t c = 0; c < R.arity; c++) {
+            if (!dcols[c]) throw Error(DL_ERR_ARG, "null column pointer");
+            t.col[c] = (uint32_t*)buf->ptr + (size_t)c * nrows;
+            DL_CUDA(cudaMemcpyAsync(t.col[c], dcols[c], sizeof(uint32_t) * nrows, cudaMemcpyDeviceToDevice, E.stream));
+        }
+        load_table(E, R, buf, t);
+    });
+}
+
+int dl_relation_clear(dl_engine* e, dl_rel_id rel) {
+    return guard(e, [&](Engine& E) {
+        Relation& R = rel_of(E, rel);
+        for (size_t k = 0; k < R.perms.size(); k++) {
+            R.full[k] = empty_index(R.arity, R.perms[k]);
+            R.delta[k] = empty_index(R.arity, R.perms[k]);
+        }
+        R.full_perms_built = true;
+        R.sink_count = 0;
+        R.sink_digest[0] = R.sink_digest[1] = 0;
+    });
+}
+
+int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,
+                uint32_t nvars, dl_rule_id* out) {
+    return guard(e, [&](Engine& E) {
+        if (!head || !body) throw Error(DL_ERR_ARG, "null head or body");
+        if (nbody == 0 || nbody > DL_MAX_BODY) throw Error(DL_ERR_ARG, "body size out of range");
+        Rule r;
+        auto read = [&](const dl_atom& a, RuleAtom& ra) {
+            Relation& R = rel_of(E, a.rel);
+            if (a.arity != R.arity) throw Error(DL_ERR_ARG, "arity mismatch for relation " + R.name);
+            if (!a.terms) throw Error(DL_ERR_ARG, "null terms");
+            ra.rel = a.rel;
+            ra.arity = a.arity;
+            for (uint32_t c = 0; c < a.arity; c++) {
+                if (a.terms[c].kind != DL_TERM_VAR && a.terms[c].kind != DL_TERM_CONST)
+                    throw Error(DL_ERR_ARG, "bad term kind");
+                if (a.terms[c].kind == DL_TERM_VAR && a.terms[c].id >= 1024) throw Error(DL_ERR_ARG, "variable id >= 1024");
+                ra.terms[c] = a.terms[c];
+            }
+        };
+        std::set<uint32_t> bvars;
+        bool unsupported_const = false, unsupported_repeat = false;
+        for (uint32_t b = 0; b < nbody; b++) {
+            RuleAtom ra;
+            read(body[b], ra);
+            std::set<uint32_t> here;
+            for (uint32_t c = 0; c < ra.arity; c++) {
+                if (ra.terms[c].kind == DL_TERM_CONST) {
+                    unsupported_const = true;
+                    continue;
+                }
+                if (!here.insert(ra.terms[c].id).second) unsupported_repeat = true;
+                bvars.insert(ra.terms[c].id);
+            }
+            r.body.push_back(ra);
+        }
+        read(*head, r.head);
+        for (uint32_t c = 0; c < r.head.arity; c++)
+            if (r.head.terms[c].kind == DL_TERM_VAR && !bvars.count(r.head.terms[c].id))
+                throw Error(DL_ERR_ARG, "head variable not bound by the body");
+        if (bvars.size() > DL_MAX_VARS) throw Error(DL_ERR_ARG, "too many variables");
+        if (!var_order || nvars != bvars.size()) throw Error(DL_ERR_ARG, "variable order must list every body variable once");
+        std::set<uint32_t> ord(var_order, var_order + nvars);
+        if (ord != bvars) throw Error(DL_ERR_ARG, "variable order is not a permutation of the body variables");
+        if (unsupported_const) throw Error(DL_ERR_UNSUPPORTED, "constants in body atoms are not supported on the GPU path");
+        if (unsupported_repeat)
+            throw Error(DL_ERR_UNSUPPORTED, "a variable repeated within one body atom is not supported on the GPU path");
+        r.order.assign(var_order, var_order + nvars);
+        for (uint32_t c = 0; c < r.head.arity; c++)
+            if (r.head.terms[c].kind == DL_TERM_CONST) {
+                if (r.head.terms[c].id == 0xffffffffu) throw Error(DL_ERR_UNSUPPORTED, "value 0xFFFFFFFF is reserved");
+                E.V = std::max(E.V, r.head.terms[c].id + 1);
+            }
+        E.rules.push_back(r);
+        if (out) *out = (dl_rule_id)(E.rules.size() - 1);
+    });
+}
+
+int dl_fixpoint(dl_engine* e, dl_stats* stats) {
+    return guard(e, [&](Engine& E) {
+        E.in_fixpoint = true;
+        try {
+            fixpoint(E, stats);
+        } catch (...) {
+            E.in_fixpoint = false;
+            throw;
+        }
+        E.in_fixpoint = false;
+    });
+}
+
+int dl_stratum_info(dl_engine* e, uint32_t s, dl_rel_id* rels, uint32_t cap, uint32_t* nrels, uint32_t* rounds) {
+    return guard(e, [&](Engine& E) {
+        if (s >= E.strata.size()) throw Error(DL_ERR_ARG, "bad stratum");
+        const Stratum& S = E.strata[s];
+        if (nrels) *nrels = (uint32_t)S.rels.size();
+        if (rounds) *rounds = S.rounds;
+        if (rels)
+            for (uint32_t i = 0; i < S.rels.size() && i < cap; i++) rels[i] = S.rels[i];
+    });
+}
+
+int dl_relation_size(dl_engine* e, dl_rel_id rel, uint64_t* nrows) {
+    return guard(e, [&](Engine& E) {
+        Relation& R = rel_of(E, rel);
+        if (!nrows) throw Error(DL_ERR_ARG, "null output");
+        *nrows = R.sink == DL_SINK_COUNT ? R.sink_count : R.full[0].n;
+    });
+}
+
+static int fetch_impl(dl_engine* e, dl_rel_id rel, uint32_t* const* cols, uint64_t cap, uint64_t* nrows, bool device) {
+    return guard(e, [&](Engine& E) {
+        Relation& R = rel_of(E, rel);
+        if (R.sink == DL_SINK_COUNT) throw Error(DL_ERR_STATE, "count sinks hold no tuples; use dl_fetch_digest");
+        const Index& ix = R.full[0];
+        if (nrows) *nrows = ix.n;
+        if (!cols) return;
+        if (cap < ix.n) throw Error(DL_ERR_ARG, "cap_rows smaller than the relation");
+        for (uint32_t c = 0; c < R.arity; c++) {
+            if (!cols[c]) throw Error(DL_ERR_ARG, "null column pointer");
+            if (ix.n)
+                DL_CUDA(cudaMemcpyAsync(cols[c], ix.col((int)c), sizeof(uint32_t) * ix.n,
+                                        device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, E.stream));
+        }
+        E.sync();
+    });
+}
+
+int dl_fetch(dl_engine* e, dl_rel_id rel, uint32_t* const* cols_out, uint64_t cap_rows, uint64_t* nrows_out) {
+    return fetch_impl(e, rel, cols_out, cap_rows, nrows_out, false);
+}
+
+int dl_fetch_device(dl_engine* e, dl_rel_id rel, uint32_t* const* dcols_out, uint64_t cap_rows, uint64_t* nrows_out) {
+    return fetch_impl(e, rel, dcols_out, cap_rows, nrows_out, true);
+}
+
+int dl_fetch_digest(dl_engine* e, dl_rel_id rel, uint64_t* count, uint64_t digest[2]) {
+    return guard(e, [&](Engine& E) {
+        Relation& R = rel_of(E, rel);
+        if (!count || !digest) throw Error(DL_ERR_ARG, "null output");
+        if (R.sink == DL_SINK_COUNT) {
+            *count = R.sink_count;
+            digest[0] = R.sink_digest[0];
+            digest[1] = R.sink_digest[1];
+            return;
+        }
+        auto d = E.array<uint64_t>(3);
+        DL_CUDA(cudaMemsetAsync(d.p, 0, 24, E.stream));
+        table_digest(E, table_of(R.full[0]), (unsigned long long*)d.p);
+        const uint64_t* h = E.readback(d.p, 3);
+        *count = h[0];
+        digest[0] = h[1];
+        digest[1] = h[2];
+    });
+}
+
+int dl_partition_slices(const uint64_t* C, uint64_t K, uint32_t p, uint64_t* first_key, uint64_t* start_unit) {
+    if (!C || !first_key || !start_unit || p == 0) return DL_ERR_ARG;
+    const uint64_t T = K ? C[K - 1] : 0;
+    const uint64_t step = (T + p - 1) / p;
+    for (uint32_t b = 0; b < p; b++) {
+        const uint64_t s = std::min<uint64_t>((uint64_t)b * step, T);
+        start_unit[b] = s;
+        first_key[b] = upper_bound_u64(C, 0, K, s);
+    }
+    return DL_OK;
+}
+
+int dl_decode_unit(const uint64_t* C, const uint64_t* d2, uint64_t K, uint64_t g, uint64_t* key, uint64_t* i1,
+                   uint64_t* i2) {
+    if (!C || !d2 || !key || !i1 || !i2 || K == 0 || g >= C[K - 1]) return DL_ERR_ARG;
+    const uint64_t k = upper_bound_u64(C, 0, K, g);
+    const uint64_t local = g - (k ? C[k - 1] : 0);
+    if (d2[k] == 0) return DL_ERR_ARG;
+    *key = k;
+    *i1 = local / d2[k];
+    *i2 = local % d2[k];
+    return DL_OK;
+}
+
+}  // extern "C"

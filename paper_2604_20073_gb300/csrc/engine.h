@@ -1,0 +1,117 @@
+// Host-side engine state (internal).
+#pragma once
+
+#include <array>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dl {
+
+using Perm = std::array<uint8_t, kMaxArity>;
+
+inline Perm identity_perm() {
+    Perm p{};
+    for (int i = 0; i < kMaxArity; i++) p[i] = (uint8_t)i;
+    return p;
+}
+
+struct Relation {
+    std::string name;
+    uint32_t arity = 0;
+    uint32_t sink = DL_SINK_STORE;
+    std::vector<Perm> perms;          // perms[0] is the identity (canonical order)
+    std::vector<Index> full;          // one index per perm; full[0] is always valid
+    std::vector<Index> delta;         // one index per perm (valid during a stratum's rounds)
+    bool full_perms_built = false;    // full[k > 0] are up to date
+    std::vector<bool> root_needed;    // per perm: build dense root offsets
+    uint64_t sink_count = 0;
+    unsigned long long sink_digest[2] = {0, 0};
+    int stratum = -1;
+};
+
+struct RuleAtom {
+    uint32_t rel = 0;
+    uint32_t arity = 0;
+    dl_term terms[kMaxArity];
+};
+
+struct Rule {
+    RuleAtom head;
+    std::vector<RuleAtom> body;
+    std::vector<uint32_t> order;      // user variable ids in join order
+};
+
+struct Stratum {
+    std::vector<uint32_t> rels;       // ascending ids
+    uint32_t rounds = 0;
+};
+
+struct PhaseEvents {                  // accumulated device time per phase kind
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+};
+
+class Engine {
+  public:
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t budget = 0, used = 0, peak = 0;
+    dl_alloc_fn ualloc = nullptr;
+    dl_free_fn ufree = nullptr;
+    void* uuser = nullptr;
+    uint32_t flags = 0;
+    uint32_t tile_units = 4096;
+    std::string err;
+    std::vector<Relation> rels;
+    std::vector<Rule> rules;
+    std::vector<Stratum> strata;
+    uint32_t V = 0;                   // values seen so far are < V
+    uint64_t* host_scratch = nullptr; // pinned, 64 words
+    uint64_t launches = 0;
+    uint64_t join_rows = 0, count_rows = 0, delta_rows = 0;
+    bool in_fixpoint = false;
+    std::vector<cudaEvent_t> event_pool;
+    size_t event_next = 0;
+    PhaseEvents phases;
+
+    ~Engine();
+    void* alloc(size_t bytes);
+    void release(void* p, size_t bytes);
+    DevPtr make(size_t bytes) { return std::make_shared<DevMem>(this, bytes); }
+    template <class T>
+    DArray<T> array(uint64_t n) {
+        DArray<T> a;
+        a.mem = make(sizeof(T) * (n ? n : 1));
+        a.p = (T*)a.mem->ptr;
+        a.n = n;
+        return a;
+    }
+    // Copy `count` uint64 words from device to host scratch and wait.
+    const uint64_t* readback(const void* dev, size_t words);
+    void sync() { DL_CUDA(cudaStreamSynchronize(stream)); }
+    cudaEvent_t next_event();
+    void phase_begin(int kind);
+    void phase_end(int kind);
+};
+
+// Allocates an index of `n` rows, `arity` columns in permutation `perm`.
+Index make_index(Engine& E, uint32_t arity, const Perm& perm, uint64_t n);
+TableView table_of(const Index& ix);
+AtomView atom_of(const Index& ix);
+
+// ---- join (wcoj.cu)
+
+struct RulePlan;
+// Evaluate one variant of a rule; src_index[k] is the index body atom k reads.  For a stored
+// head the output rows (head column order) are appended to `out_parts`; for a count sink the
+// counts go to the relation's sink counters.
+struct JoinOutput {
+    std::vector<TableView> parts;     // each part: arity columns
+    std::vector<DevPtr> owners;
+    bool sorted_unique = true;        // rows of each part are sorted (canonical) and distinct
+};
+void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Relation& head, JoinOutput& out);
+
+}  // namespace dl

@@ -1,0 +1,457 @@
+// Data-parallel primitives of the semi-naive loop: device prefix scan, LSD radix sort of
+// SoA rows, adjacent dedup + anti-join against the full relation (Compute Delta), merge-path
+// merge (Merge), dense root offsets (Build Index), digests.
+//
+// Paper context: Section 4 names the phases Compute Delta (filter new tuples against the
+// full relation), Build Index (sort new tuples into lexicographic SoA order) and Merge
+// (single-pass GPU merge path, Green et al. 2012); Algorithm 1 uses prefix sums for the
+// work histogram and for the count -> offset step.
+#include <algorithm>
+#include <cstring>
+
+#include "engine.h"
+
+namespace dl {
+
+namespace {
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Block-wide exclusive scan of one value per thread; *total gets the block sum.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T& total) {
+    __shared__ T warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    T x = warp_inclusive_scan(v);
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nwarps ? warp_sums[lane] : T(0);
+        w = warp_inclusive_scan(w);
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    T prefix = warp ? warp_sums[warp - 1] : T(0);
+    total = warp_sums[nwarps - 1];
+    __syncthreads();
+    return prefix + x - v;
+}
+
+template <typename T>
+__global__ void k_scan_reduce(const T* __restrict__ in, uint64_t n, T* __restrict__ sums) {
+    uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++)
+        if (base + k < n) s += in[base + k];
+    T total;
+    block_exclusive_scan(s, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+template <typename T>
+__global__ void k_scan_down(T* __restrict__ data, uint64_t n, const T* __restrict__ offs, bool inclusive,
+                            uint64_t* total_out) {
+    uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        v[k] = base + k < n ? data[base + k] : T(0);
+        s += v[k];
+    }
+    T total;
+    T run = block_exclusive_scan(s, total) + (offs ? offs[blockIdx.x] : T(0));
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        T x = v[k];
+        if (base + k < n) data[base + k] = inclusive ? run + x : run;
+        run += x;
+    }
+    if (total_out && threadIdx.x == 0) *total_out = (uint64_t)total;
+}
+
+template <typename T>
+void scan_impl(Engine& E, T* data, uint64_t n, bool inclusive, uint64_t* total_dev) {
+    if (n == 0) {
+        if (total_dev) DL_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), E.stream));
+        return;
+    }
+    uint64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 1) {
+        k_scan_down<T><<<1, kScanThreads, 0, E.stream>>>(data, n, nullptr, inclusive, total_dev);
+        DL_CHECK_LAUNCH();
+        E.launches++;
+        return;
+    }
+    auto sums = E.array<T>(nb);
+    k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, E.stream>>>(data, n, sums.p);
+    DL_CHECK_LAUNCH();
+    E.launches++;
+    scan_impl<T>(E, sums.p, nb, false, total_dev);
+    k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, E.stream>>>(data, n, sums.p, inclusive, nullptr);
+    DL_CHECK_LAUNCH();
+    E.launches++;
+}
+
+// ------------------------------------------------------------------ radix sort
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void k_varying_bits(const uint32_t* __restrict__ col, uint64_t n, uint32_t* out) {
+    uint32_t first = col[0];
+    uint32_t acc = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        acc |= col[i] ^ first;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc |= __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicOr(out, acc);
+}
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ key, uint64_t n, uint32_t shift,
+                             uint32_t* __restrict__ hist, uint32_t ntiles) {
+    __shared__ uint32_t h[kRadix];
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    for (int j = threadIdx.x; j < kSortTile; j += blockDim.x) {
+        uint64_t i = base + j;
+        uint32_t d = i < n ? (key[i] >> shift) & (kRadix - 1) : 0xffffffffu;
+        unsigned peers = __match_any_sync(kFull, d);
+        if (i < n && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(uint64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+// Stable scatter: warp w of the block owns the contiguous rows [base + w*32*I, base + (w+1)*32*I);
+// iteration j handles row base + w*32*I + j*32 + lane, so (j, lane) order is row order.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(TableView src, TableView dst, int keycol,
+                                                                uint32_t shift, const uint32_t* __restrict__ offs,
+                                                                uint32_t ntiles) {
+    __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t n = src.n;
+    const uint64_t wbase = (uint64_t)blockIdx.x * kSortTile + (uint64_t)warp * 32 * kSortItems;
+    const unsigned lt = (1u << lane) - 1;
+    uint32_t rank[kSortItems], dig[kSortItems];
+    const uint32_t* key = src.col[keycol];
+#pragma unroll
+    for (int j = 0; j < kSortItems; j++) {
+        uint64_t i = wbase + (uint64_t)j * 32 + lane;
+        bool valid = i < n;
+        uint32_t d = valid ? (key[i] >> shift) & (kRadix - 1) : 0xffffffffu;
+        unsigned peers = __match_any_sync(kFull, d);
+        uint32_t before = valid ? wcnt[warp][d] : 0;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[j] = before + __popc(peers & lt);
+        dig[j] = d;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+        uint32_t run = offs[(uint64_t)d * ntiles + blockIdx.x];
+        for (int w = 0; w < kSortWarps; w++) {
+            uint32_t c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortItems; j++) {
+        uint64_t i = wbase + (uint64_t)j * 32 + lane;
+        if (i < n) {
+            uint64_t to = (uint64_t)wcnt[warp][dig[j]] + rank[j];
+            for (uint32_t c = 0; c < src.arity; c++) dst.col[c][to] = src.col[c][i];
+        }
+    }
+}
+
+// ------------------------------------------------------------- compaction
+
+constexpr int kCompThreads = 256;
+constexpr int kCompItems = 16;
+constexpr int kCompTile = kCompThreads * kCompItems;
+
+__device__ __forceinline__ bool row_equal(const TableView& t, uint64_t i, uint64_t j) {
+    for (uint32_t c = 0; c < t.arity; c++)
+        if (t.col[c][i] != t.col[c][j]) return false;
+    return true;
+}
+
+__device__ bool contains_row(const AtomView& a, const TableView& t, uint64_t i) {
+    uint32_t lo = 0, hi = a.n;
+    for (uint32_t c = 0; c < a.arity; c++)
+        if (!narrow(a, (int)c, t.col[c][i], lo, hi)) return false;
+    return true;
+}
+
+struct UniqueAnti {
+    TableView in;
+    AtomView full;
+    bool use_full;
+    __device__ bool operator()(uint64_t i) const {
+        if (i > 0 && row_equal(in, i, i - 1)) return false;
+        return !use_full || !contains_row(full, in, i);
+    }
+};
+
+template <class Pred>
+__global__ void k_flag_count(Pred pred, uint64_t n, uint64_t* __restrict__ block_count) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    uint64_t c = 0;
+    for (int j = threadIdx.x; j < kCompTile; j += blockDim.x) {
+        uint64_t i = base + j;
+        if (i < n && pred(i)) c++;
+    }
+    uint64_t total;
+    block_exclusive_scan(c, total);
+    if (threadIdx.x == 0) block_count[blockIdx.x] = total;
+}
+
+template <class Pred>
+__global__ void k_flag_write(Pred pred, TableView in, TableView out, const uint64_t* __restrict__ block_off) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    uint64_t run = block_off[blockIdx.x];
+    for (int j = 0; j < kCompItems; j++) {
+        uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+        uint32_t f = (i < in.n && pred(i)) ? 1u : 0u;
+        uint32_t total;
+        uint32_t pos = block_exclusive_scan(f, total);
+        if (f)
+            for (uint32_t c = 0; c < in.arity; c++) out.col[c][run + pos] = in.col[c][i];
+        run += total;
+    }
+}
+
+// ------------------------------------------------------------------ merge
+
+constexpr int kMergeThreads = 256;
+constexpr int kMergeItems = 8;
+
+// lexicographic a[i] < b[j]
+__device__ __forceinline__ bool row_less(const TableView& a, uint64_t i, const TableView& b, uint64_t j) {
+    for (uint32_t c = 0; c < a.arity; c++) {
+        uint32_t x = a.col[c][i], y = b.col[c][j];
+        if (x != y) return x < y;
+    }
+    return false;
+}
+
+__global__ void k_merge(TableView a, TableView b, TableView out) {
+    const uint64_t total = a.n + b.n;
+    const uint64_t diag = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kMergeItems;
+    if (diag >= total) return;
+    // merge path: number of a-rows among the first `diag` outputs (a first on ties)
+    uint64_t lo = diag > b.n ? diag - b.n : 0, hi = diag < a.n ? diag : a.n;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (!row_less(b, diag - 1 - mid, a, mid)) lo = mid + 1; else hi = mid;
+    }
+    uint64_t i = lo, j = diag - lo;
+    const uint64_t end = min(diag + kMergeItems, total);
+    for (uint64_t k = diag; k < end; k++) {
+        bool take_a = j >= b.n || (i < a.n && !row_less(b, j, a, i));
+        if (take_a) {
+            for (uint32_t c = 0; c < a.arity; c++) out.col[c][k] = a.col[c][i];
+            i++;
+        } else {
+            for (uint32_t c = 0; c < a.arity; c++) out.col[c][k] = b.col[c][j];
+            j++;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ misc
+
+__global__ void k_build_root(const uint32_t* __restrict__ col0, uint32_t n, uint32_t* __restrict__ root, uint32_t V) {
+    uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (v > V) return;
+    root[v] = v == V ? n : lower_bound_u32(col0, 0, n, (uint32_t)v);
+}
+
+__global__ void k_column_max(const uint32_t* __restrict__ col, uint64_t n, uint32_t* out) {
+    uint32_t m = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        m = max(m, col[i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_digest(TableView t, unsigned long long* d) {
+    unsigned long long s = 0, x = 0, c = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < t.n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t h = kTupleHashSeed;
+        for (uint32_t j = 0; j < t.arity; j++) h = tuple_hash_step(h, t.col[j][i], j);
+        s += h;
+        x ^= h;
+        c++;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(kFull, s, o);
+        x ^= __shfl_xor_sync(kFull, x, o);
+        c += __shfl_xor_sync(kFull, c, o);
+    }
+    if ((threadIdx.x & 31) == 0 && c) {
+        atomicAdd(&d[0], c);
+        atomicAdd(&d[1], s);
+        atomicXor(&d[2], x);
+    }
+}
+
+__global__ void k_order_violations(TableView t, unsigned long long* out) {
+    unsigned long long c = 0;
+    for (uint64_t i = 1 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < t.n; i += (uint64_t)gridDim.x * blockDim.x)
+        if (!row_less(t, i - 1, t, i)) c++;
+    if (c) atomicAdd(out, c);
+}
+
+unsigned grid_for(uint64_t n, int threads, unsigned cap = 152u * 16u) {
+    uint64_t g = (n + threads - 1) / threads;
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, cap));
+}
+
+}  // namespace
+
+void scan_u64(Engine& E, uint64_t* data, uint64_t n, bool inclusive, uint64_t* total_dev) {
+    scan_impl<unsigned long long>(E, (unsigned long long*)data, n, inclusive, total_dev);
+}
+
+void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev) {
+    scan_impl<uint32_t>(E, data, n, false, total_dev);
+}
+
+void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out) {
+    int passes = 0;
+    const uint64_t n = t.n;
+    if (n > 1) {
+        if (n >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "sort of 2^32 rows or more");
+        auto bits = E.array<uint32_t>(kMaxArity);
+        DL_CUDA(cudaMemsetAsync(bits.p, 0, sizeof(uint32_t) * kMaxArity, E.stream));
+        for (uint32_t c = 0; c < t.arity; c++) {
+            k_varying_bits<<<grid_for(n, 256), 256, 0, E.stream>>>(t.col[c], n, bits.p + c);
+            DL_CHECK_LAUNCH();
+            E.launches++;
+        }
+        uint32_t hbits[kMaxArity];
+        const uint64_t* hb = E.readback(bits.p, kMaxArity / 2);
+        memcpy(hbits, hb, sizeof(uint32_t) * t.arity);
+        const uint32_t ntiles = (uint32_t)((n + kSortTile - 1) / kSortTile);
+        auto hist = E.array<uint32_t>((uint64_t)kRadix * ntiles);
+        for (int c = (int)t.arity - 1; c >= 0; c--) {
+            uint32_t vb = hbits[c];
+            if (!vb) continue;
+            int lo = __builtin_ctz(vb), hi = 31 - __builtin_clz(vb);
+            for (int shift = lo; shift <= hi; shift += kRadixBits) {
+                k_radix_hist<<<ntiles, kSortThreads, 0, E.stream>>>(t.col[c], n, shift, hist.p, ntiles);
+                DL_CHECK_LAUNCH();
+                scan_u32(E, hist.p, (uint64_t)kRadix * ntiles, nullptr);
+                TableView dst = tmp;
+                dst.n = n;
+                k_radix_scatter<<<ntiles, kSortThreads, 0, E.stream>>>(t, dst, c, shift, hist.p, ntiles);
+                DL_CHECK_LAUNCH();
+                E.launches += 2;
+                std::swap(t, tmp);
+                t.n = n;
+                passes++;
+            }
+        }
+    }
+    if (passes_out) *passes_out = passes;
+}
+
+uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const TableView& out) {
+    const uint64_t n = in.n;
+    if (n == 0) return 0;
+    UniqueAnti pred;
+    pred.in = in;
+    pred.use_full = full && full->n > 0;
+    if (full) pred.full = *full; else memset(&pred.full, 0, sizeof(pred.full));
+    const uint64_t nb = (n + kCompTile - 1) / kCompTile;
+    auto cnt = E.array<uint64_t>(nb + 1);
+    k_flag_count<UniqueAnti><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, n, cnt.p);
+    DL_CHECK_LAUNCH();
+    scan_u64(E, cnt.p, nb, false, cnt.p + nb);
+    const uint64_t total = E.readback(cnt.p + nb, 1)[0];
+    if (total) {
+        k_flag_write<UniqueAnti><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, in, out, cnt.p);
+        DL_CHECK_LAUNCH();
+        E.launches++;
+    }
+    E.launches++;
+    return total;
+}
+
+void merge_rows(Engine& E, const TableView& a, const TableView& b, const TableView& out) {
+    const uint64_t total = a.n + b.n;
+    if (!total) return;
+    const uint64_t threads = (total + kMergeItems - 1) / kMergeItems;
+    k_merge<<<(unsigned)((threads + kMergeThreads - 1) / kMergeThreads), kMergeThreads, 0, E.stream>>>(a, b, out);
+    DL_CHECK_LAUNCH();
+    E.launches++;
+}
+
+void build_root(Engine& E, const uint32_t* col0, uint64_t n, uint32_t* root, uint32_t V) {
+    const uint64_t cnt = (uint64_t)V + 1;
+    k_build_root<<<(unsigned)((cnt + 255) / 256), 256, 0, E.stream>>>(col0, (uint32_t)n, root, V);
+    DL_CHECK_LAUNCH();
+    E.launches++;
+}
+
+void column_max(Engine& E, const uint32_t* col, uint64_t n, uint32_t* out_dev) {
+    if (!n) return;
+    k_column_max<<<grid_for(n, 256), 256, 0, E.stream>>>(col, n, out_dev);
+    DL_CHECK_LAUNCH();
+    E.launches++;
+}
+
+void table_digest(Engine& E, const TableView& t, unsigned long long* d) {
+    if (!t.n) return;
+    k_digest<<<grid_for(t.n, 256), 256, 0, E.stream>>>(t, d);
+    DL_CHECK_LAUNCH();
+    E.launches++;
+}
+
+void permute_copy(Engine& E, const TableView& in, const uint8_t* perm, const TableView& out) {
+    for (uint32_t k = 0; k < in.arity; k++)
+        if (in.n)
+            DL_CUDA(cudaMemcpyAsync(out.col[k], in.col[perm[k]], sizeof(uint32_t) * in.n, cudaMemcpyDeviceToDevice,
+                                    E.stream));
+}
+
+uint64_t count_order_violations(Engine& E, const TableView& t) {
+    if (t.n < 2) return 0;
+    auto c = E.array<uint64_t>(1);
+    DL_CUDA(cudaMemsetAsync(c.p, 0, 8, E.stream));
+    k_order_violations<<<grid_for(t.n, 256), 256, 0, E.stream>>>(t, (unsigned long long*)c.p);
+    DL_CHECK_LAUNCH();
+    E.launches++;
+    return E.readback(c.p, 1)[0];
+}
+
+}  // namespace dl
