@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Benchmark: WCOJ tuples/s of a full semi-naive fixpoint on the skewed cyclic workload.
+
+Workload: R-MAT scale 20 (1,048,576 nodes, a = 0.57, b = c = 0.19, d = 0.05, seed 1001),
+symmetrised: 8,388,608 distinct unordered pairs, both directions, 16,777,216 uint32 rows in
+E.  Program: Tri(x,y,z) :- E(x,y), E(y,z), E(x,z) (stored) and
+Q4(w,x,y,z) :- E(w,x), E(w,y), E(w,z), E(x,y), E(x,z), E(y,z) (count sink: its ~5e10 rows
+do not fit in memory; it is counted and digested), variable orders x<y<z and w<x<y<z.
+
+One step = one dl_fixpoint call over E already resident in HBM (both strata: histogram,
+count, scan, write, delta and merge phases).  value = join output tuples (Tri + Q4) per
+second.  e2e = the same metric through the C ABI from pinned HOST buffers: load E (H2D and
+index build), fixpoint, fetch Tri to the host (D2H) and the Q4 digest, all timed.
+
+`--impl reference` times the CPU oracle (the reference arm of this repository) on a
+bounded root sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+UNIT = "tuples/s"
+FALLBACK_HBM_GBS = 6800.0
+
+TRI = [(("Tri", ["x", "y", "z"]), [("E", ["x", "y"]), ("E", ["y", "z"]), ("E", ["x", "z"])], ["x", "y", "z"])]
+Q4 = [(("Q4", ["w", "x", "y", "z"]),
+       [("E", ["w", "x"]), ("E", ["w", "y"]), ("E", ["w", "z"]), ("E", ["x", "y"]), ("E", ["x", "z"]), ("E", ["y", "z"])],
+       ["w", "x", "y", "z"])]
+# Root-restricted forms for the CPU oracle's bounded sample (same result rows for the sampled
+# roots; atoms listed in an order that keeps the oracle's left-deep plan small).
+TRI_S = [(("Tri", ["x", "y", "z"]), [("Root", ["x"]), ("E", ["x", "y"]), ("E", ["y", "z"]), ("E", ["x", "z"])])]
+Q4_S = [(("Q4", ["w", "x", "y", "z"]),
+         [("Root", ["w"]), ("E", ["w", "x"]), ("E", ["w", "y"]), ("E", ["x", "y"]), ("E", ["w", "z"]),
+          ("E", ["x", "z"]), ("E", ["y", "z"])])]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def metric_name(scale):
+    return f"WCOJ tuples/s (Tri + 4-clique fixpoint, symmetrised R-MAT scale {scale})"
+
+
+def workload(scale):
+    from paper_2604_20073_gb300 import datagen as dg
+    n = 1 << scale
+    e = dg.rmat_edges(n, 16 * n, 1001, symmetric=True)
+    cfg = {"workload": f"skewed cyclic WCOJ: Tri + Q4 on symmetrised R-MAT scale {scale}",
+           "nodes": n, "edges": int(e.shape[0]), "rmat": [0.57, 0.19, 0.19, 0.05], "seed": 1001,
+           "orders": {"Tri": "x<y<z", "Q4": "w<x<y<z"}, "q4_sink": "count+digest",
+           "l2": "flushed between timed steps (512 MiB write)"}
+    return e, cfg
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        loaded = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_for(kernel_kind):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the
+    kernel's source has not changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+        ent = d[kernel_kind]
+        src = open(os.path.join(ROOT, "paper_2604_20073_gb300", "csrc", ent["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != ent["source_sha256"]:
+            return None
+        return ent["dram_bytes_per_launch_fullsize"]
+    except Exception:
+        return None
+
+
+def cpu_baseline(e, target_s):
+    """The oracle, as it stands, on a bounded sample: all Tri and Q4 rows rooted at a
+    random sample of vertices (doubling the sample until one run takes >= target_s)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(7)
+    verts = np.unique(e[:, 0])
+    k = 64
+    while True:
+        roots = np.sort(rng.choice(verts, size=min(k, len(verts)), replace=False)).astype(np.uint32).reshape(-1, 1)
+        t0 = time.perf_counter()
+        r = oracle.evaluate({"E": 2, "Root": 1, "Tri": 3, "Q4": 4}, {"E": e, "Root": roots}, TRI_S + Q4_S)
+        dt = time.perf_counter() - t0
+        tuples = len(r.relations["Tri"]) + len(r.relations["Q4"])
+        if dt >= target_s or k >= len(verts):
+            return {"value": tuples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"Tri+Q4 rows rooted at {len(roots)} random vertices ({tuples} tuples, {dt:.1f} s, "
+                              f"1 thread, left-deep hash-indexed nested loops)"}
+        k *= 2
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    e, cfg = workload(args.scale)
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(11)
+    verts = np.unique(e[:, 0])
+    roots = np.sort(rng.choice(verts, size=min(256, len(verts)), replace=False)).astype(np.uint32).reshape(-1, 1)
+    times, tuples = [], 0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.evaluate({"E": 2, "Root": 1, "Tri": 3, "Q4": 4}, {"E": e, "Root": roots}, TRI_S + Q4_S)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            tuples = len(r.relations["Tri"]) + len(r.relations["Q4"])
+    ms = 1e3 * statistics.mean(times)
+    val = tuples / (ms / 1e3)
+    sample = f"Tri+Q4 rows rooted at {len(roots)} random vertices per step ({tuples} tuples), 1 thread"
+    print(json.dumps({"impl": "reference", "metric": metric_name(args.scale), "value": val, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
+                      "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_2604_20073_gb300 as pkg
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    from paper_2604_20073_gb300.build import build_library
+    if not os.path.exists(pkg.LIB_PATH):
+        build_library()
+    e, cfg = workload(args.scale)
+    dev = torch.device("cuda", local)
+    eng = pkg.Engine(device=local, flags=pkg.DL_FLAG_PROFILE)
+    pkg.build_program(eng, {"E": 2, "Tri": 3, "Q4": 4}, TRI + Q4, {"Q4": pkg.DL_SINK_COUNT})
+    e_dev = torch.from_numpy(np.ascontiguousarray(e.T)).to(dev)       # (2, m) resident columns
+    eng.load("E", e_dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        eng.clear("Tri")
+        eng.clear("Q4")
+        return eng.fixpoint()
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    clocks = Clocks(local)
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        barrier()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        times.append(a.elapsed_time(b))
+        stats.append(st)
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    tuples = stats[-1]["join_rows"] + stats[-1]["count_rows"]
+    value = world * tuples / (ms / 1e3)
+
+    # dominant kernel over the timed region (events on the engine's stream)
+    agg = {k: {"launches": 0, "ms": 0.0, "alg_bytes": 0} for k in pkg.KERNEL_KINDS}
+    for st in stats:
+        for k, v in st["kernels"].items():
+            for f in ("launches", "ms", "alg_bytes"):
+                agg[k][f] += v[f]
+    dom = max(agg, key=lambda k: agg[k]["ms"])
+    peak, peak_kind = measured_peak()
+    d = agg[dom]
+    achieved = (d["alg_bytes"] / d["launches"]) / (d["ms"] / d["launches"] / 1e3) / 1e9 if d["launches"] else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_source": peak_kind,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom),
+                "alg_bytes_per_launch": d["alg_bytes"] / max(1, d["launches"]),
+                "avg_launch_ms": d["ms"] / max(1, d["launches"]),
+                "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in agg.items() if v["launches"]}}
+
+    # end to end through the C ABI from pinned host buffers
+    e_host = [torch.from_numpy(np.ascontiguousarray(e[:, c])).pin_memory().numpy() for c in range(2)]
+    ntri = eng.size("Tri")
+    tri_host = [torch.empty(ntri, dtype=torch.int32).pin_memory().numpy().view(np.uint32) for _ in range(3)]
+    e2e_times = []
+    for _ in range(max(1, min(2, args.steps))):
+        for r in ("E", "Tri", "Q4"):
+            eng.clear(r)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eng.lib.dl_load_facts(eng.h, eng.rel_ids["E"], pkg._cols_ptrs(e_host), len(e))
+        st = eng.fixpoint()
+        got = eng.fetch_into("Tri", tri_host)
+        dg = eng.digest("Q4")
+        e2e_times.append(time.perf_counter() - t0)
+        assert got == ntri and dg[0] == stats[-1]["count_rows"]
+    e2e_s = statistics.mean(e2e_times)
+    e2e = {"value": world * tuples / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(e.nbytes),
+           "d2h_bytes_per_step": int(ntri * 12 + 24), "ms_per_step": 1e3 * e2e_s}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(e, args.cpu_seconds)
+    if rank == 0:
+        launches = sum(st["kernel_launches"] for st in stats)
+        out = {"metric": metric_name(args.scale), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
+               "results": {"Tri_rows": int(stats[-1]["join_rows"]), "Q4_rows": int(stats[-1]["count_rows"]),
+                           "rounds": stats[-1]["rounds"], "peak_bytes": int(stats[-1]["peak_bytes"])},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(out))
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

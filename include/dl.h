@@ -52,6 +52,7 @@ extern "C" {
 #define DL_FLAG_NAIVE_ROOTS 0x1u  /* A/B baseline: one root key per work group, no histogram split
                                      (the naive assignment ablated in Section 7.3) */
 #define DL_FLAG_DEBUG_CHECKS 0x2u /* re-verify sortedness/uniqueness of every index after each round */
+#define DL_FLAG_PROFILE 0x4u      /* time every kernel launch with CUDA events (dl_stats.kernels) */
 
 typedef struct dl_engine dl_engine;
 typedef uint32_t dl_rel_id;
@@ -159,6 +160,23 @@ int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t
 
 /* ------------------------------------------------------------------ fixpoint */
 
+/* Kernel kinds reported in dl_stats.kernels (filled when DL_FLAG_PROFILE is set). */
+#define DL_K_JOIN_HIST 0      /* per-level work histogram (Algorithm 1, Phase 1) */
+#define DL_K_JOIN_COUNT 1     /* count pass (Algorithm 1, Phase 2) */
+#define DL_K_JOIN_WRITE 2     /* write pass (Algorithm 1, Phase 3) */
+#define DL_K_SCAN 3           /* device prefix scans */
+#define DL_K_SORT 4           /* radix-sort histogram + scatter passes (Build Index) */
+#define DL_K_DELTA 5          /* dedup + anti-join against the full relation (Compute Delta) */
+#define DL_K_MERGE 6          /* merge path (Merge) */
+#define DL_K_OTHER 7          /* root offsets, digests, reductions */
+#define DL_KERNEL_KINDS 8
+
+typedef struct dl_kernel_stat {
+    uint64_t launches;        /* launches of this kind during the call */
+    double ms;                /* summed device time (CUDA events on the engine's stream) */
+    uint64_t alg_bytes;       /* algorithmic bytes the launches had to move */
+} dl_kernel_stat;
+
 typedef struct dl_stats {
     uint32_t nstrata;                        /* strata evaluated (relations derived by rules) */
     uint32_t rounds[DL_MAX_STRATA];          /* rounds of each stratum, in evaluation order */
@@ -174,6 +192,7 @@ typedef struct dl_stats {
     double ms_sort;            /* device time of delta radix sorts */
     double ms_dedup;           /* device time of dedup + anti-join (compute delta) */
     double ms_merge;           /* device time of merges and index rebuilds */
+    dl_kernel_stat kernels[DL_KERNEL_KINDS];  /* per kernel kind; zero unless DL_FLAG_PROFILE */
 } dl_stats;
 
 /* Evaluate all rules to the least fixpoint (semi-naive, Jacobi rounds: every rule of a

@@ -30,6 +30,8 @@ ERR_NAMES = {1: "DL_ERR_ARG", 2: "DL_ERR_UNSUPPORTED", 3: "DL_ERR_CAPACITY", 4: 
              5: "DL_ERR_TIMEOUT", 6: "DL_ERR_STATE"}
 DL_FLAG_NAIVE_ROOTS = 0x1
 DL_FLAG_DEBUG_CHECKS = 0x2
+DL_FLAG_PROFILE = 0x4
+KERNEL_KINDS = ["join_hist", "join_count", "join_write", "scan", "sort", "delta", "merge", "other"]
 DL_SINK_STORE, DL_SINK_COUNT = 0, 1
 DL_TERM_VAR, DL_TERM_CONST = 0, 1
 DL_MAX_STRATA = 64
@@ -55,13 +57,18 @@ class dl_atom(ctypes.Structure):
     _fields_ = [("rel", ctypes.c_uint32), ("arity", ctypes.c_uint32), ("terms", ctypes.POINTER(dl_term))]
 
 
+class dl_kernel_stat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("alg_bytes", ctypes.c_uint64)]
+
+
 class dl_stats(ctypes.Structure):
     _fields_ = [("nstrata", ctypes.c_uint32), ("rounds", ctypes.c_uint32 * DL_MAX_STRATA),
                 ("stratum_first_rel", ctypes.c_uint32 * DL_MAX_STRATA), ("total_rounds", ctypes.c_uint32),
                 ("join_rows", ctypes.c_uint64), ("count_rows", ctypes.c_uint64), ("delta_rows", ctypes.c_uint64),
                 ("peak_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
                 ("ms_total", ctypes.c_double), ("ms_join", ctypes.c_double), ("ms_sort", ctypes.c_double),
-                ("ms_dedup", ctypes.c_double), ("ms_merge", ctypes.c_double)]
+                ("ms_dedup", ctypes.c_double), ("ms_merge", ctypes.c_double),
+                ("kernels", dl_kernel_stat * len(KERNEL_KINDS))]
 
 
 _lock = threading.Lock()
@@ -249,8 +256,10 @@ class Engine:
     def fixpoint(self) -> dict:
         st = dl_stats()
         self._check(self.lib.dl_fixpoint(self.h, ctypes.byref(st)))
-        out = {f: getattr(st, f) for f, _ in dl_stats._fields_ if f not in ("rounds", "stratum_first_rel")}
+        out = {f: getattr(st, f) for f, _ in dl_stats._fields_ if f not in ("rounds", "stratum_first_rel", "kernels")}
         out["rounds"] = list(st.rounds[: min(st.nstrata, DL_MAX_STRATA)])
+        out["kernels"] = {k: {"launches": st.kernels[i].launches, "ms": st.kernels[i].ms,
+                              "alg_bytes": st.kernels[i].alg_bytes} for i, k in enumerate(KERNEL_KINDS)}
         return out
 
     def strata(self) -> list:

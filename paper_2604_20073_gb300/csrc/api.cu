@@ -469,6 +469,9 @@ void fixpoint(Engine& E, dl_stats* st) {
     E.peak = E.used;
     E.event_next = 0;
     for (auto& v : E.phases.ev) v.clear();
+    E.kev.clear();
+    uint64_t klaunch0[DL_KERNEL_KINDS];
+    memcpy(klaunch0, E.klaunch, sizeof(klaunch0));
     validate_program(E);
     // plan: index permutations each atom reads; roots for every index a join probes
     for (const Rule& r : E.rules)
@@ -560,6 +563,12 @@ void fixpoint(Engine& E, dl_stats* st) {
                 float f = 0;
                 if (pr.second && cudaEventElapsedTime(&f, pr.first, pr.second) == cudaSuccess) *ms[k] += f;
             }
+        for (int k = 0; k < DL_KERNEL_KINDS; k++) st->kernels[k].launches = E.klaunch[k] - klaunch0[k];
+        for (const KernelEvent& ke : E.kev) {
+            float f = 0;
+            if (cudaEventElapsedTime(&f, ke.a, ke.b) == cudaSuccess) st->kernels[ke.kind].ms += f;
+            st->kernels[ke.kind].alg_bytes += ke.bytes;
+        }
         st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
 }

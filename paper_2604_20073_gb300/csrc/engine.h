@@ -52,6 +52,12 @@ struct PhaseEvents {                  // accumulated device time per phase kind
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
 };
 
+struct KernelEvent {
+    int kind;
+    cudaEvent_t a, b;
+    uint64_t bytes;
+};
+
 class Engine {
   public:
     int device = 0;
@@ -75,6 +81,8 @@ class Engine {
     std::vector<cudaEvent_t> event_pool;
     size_t event_next = 0;
     PhaseEvents phases;
+    std::vector<KernelEvent> kev;     // DL_FLAG_PROFILE: one entry per timed launch
+    uint64_t klaunch[DL_KERNEL_KINDS] = {0};
 
     ~Engine();
     void* alloc(size_t bytes);
@@ -94,6 +102,30 @@ class Engine {
     cudaEvent_t next_event();
     void phase_begin(int kind);
     void phase_end(int kind);
+};
+
+// Times one kernel launch (or a short sequence) of a given kind when profiling is enabled,
+// and counts launches of that kind in every case.
+struct KernelScope {
+    Engine& E;
+    int kind;
+    uint64_t bytes;
+    cudaEvent_t a = nullptr;
+    KernelScope(Engine& e, int k, uint64_t b, int nlaunch = 1) : E(e), kind(k), bytes(b) {
+        E.launches += nlaunch;
+        E.klaunch[k] += nlaunch;
+        if (E.flags & DL_FLAG_PROFILE) {
+            a = E.next_event();
+            cudaEventRecord(a, E.stream);
+        }
+    }
+    ~KernelScope() {
+        if (a) {
+            cudaEvent_t b = E.next_event();
+            cudaEventRecord(b, E.stream);
+            E.kev.push_back({kind, a, b, bytes});
+        }
+    }
 };
 
 // Allocates an index of `n` rows, `arity` columns in permutation `perm`.

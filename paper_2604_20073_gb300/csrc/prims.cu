@@ -93,19 +93,21 @@ void scan_impl(Engine& E, T* data, uint64_t n, bool inclusive, uint64_t* total_d
     }
     uint64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb == 1) {
+        KernelScope ks(E, DL_K_SCAN, 2 * sizeof(T) * n);
         k_scan_down<T><<<1, kScanThreads, 0, E.stream>>>(data, n, nullptr, inclusive, total_dev);
         DL_CHECK_LAUNCH();
-        E.launches++;
         return;
     }
     auto sums = E.array<T>(nb);
-    k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, E.stream>>>(data, n, sums.p);
-    DL_CHECK_LAUNCH();
-    E.launches++;
+    {
+        KernelScope ks(E, DL_K_SCAN, sizeof(T) * n);
+        k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, E.stream>>>(data, n, sums.p);
+        DL_CHECK_LAUNCH();
+    }
     scan_impl<T>(E, sums.p, nb, false, total_dev);
+    KernelScope ks(E, DL_K_SCAN, 2 * sizeof(T) * n);
     k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, E.stream>>>(data, n, sums.p, inclusive, nullptr);
     DL_CHECK_LAUNCH();
-    E.launches++;
 }
 
 // ------------------------------------------------------------------ radix sort
@@ -354,9 +356,9 @@ void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out) {
         auto bits = E.array<uint32_t>(kMaxArity);
         DL_CUDA(cudaMemsetAsync(bits.p, 0, sizeof(uint32_t) * kMaxArity, E.stream));
         for (uint32_t c = 0; c < t.arity; c++) {
+            KernelScope ks(E, DL_K_SORT, 4 * n);
             k_varying_bits<<<grid_for(n, 256), 256, 0, E.stream>>>(t.col[c], n, bits.p + c);
             DL_CHECK_LAUNCH();
-            E.launches++;
         }
         uint32_t hbits[kMaxArity];
         const uint64_t* hb = E.readback(bits.p, kMaxArity / 2);
@@ -368,14 +370,17 @@ void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out) {
             if (!vb) continue;
             int lo = __builtin_ctz(vb), hi = 31 - __builtin_clz(vb);
             for (int shift = lo; shift <= hi; shift += kRadixBits) {
-                k_radix_hist<<<ntiles, kSortThreads, 0, E.stream>>>(t.col[c], n, shift, hist.p, ntiles);
-                DL_CHECK_LAUNCH();
+                {
+                    KernelScope ks(E, DL_K_SORT, 4 * n);
+                    k_radix_hist<<<ntiles, kSortThreads, 0, E.stream>>>(t.col[c], n, shift, hist.p, ntiles);
+                    DL_CHECK_LAUNCH();
+                }
                 scan_u32(E, hist.p, (uint64_t)kRadix * ntiles, nullptr);
                 TableView dst = tmp;
                 dst.n = n;
+                KernelScope ks(E, DL_K_SORT, (4 + 8ull * t.arity) * n);
                 k_radix_scatter<<<ntiles, kSortThreads, 0, E.stream>>>(t, dst, c, shift, hist.p, ntiles);
                 DL_CHECK_LAUNCH();
-                E.launches += 2;
                 std::swap(t, tmp);
                 t.n = n;
                 passes++;
@@ -394,16 +399,19 @@ uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const
     if (full) pred.full = *full; else memset(&pred.full, 0, sizeof(pred.full));
     const uint64_t nb = (n + kCompTile - 1) / kCompTile;
     auto cnt = E.array<uint64_t>(nb + 1);
-    k_flag_count<UniqueAnti><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, n, cnt.p);
-    DL_CHECK_LAUNCH();
+    const uint64_t rowb = 4ull * in.arity;
+    {
+        KernelScope ks(E, DL_K_DELTA, 2 * rowb * n);
+        k_flag_count<UniqueAnti><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, n, cnt.p);
+        DL_CHECK_LAUNCH();
+    }
     scan_u64(E, cnt.p, nb, false, cnt.p + nb);
     const uint64_t total = E.readback(cnt.p + nb, 1)[0];
     if (total) {
+        KernelScope ks(E, DL_K_DELTA, 2 * rowb * n + rowb * total);
         k_flag_write<UniqueAnti><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, in, out, cnt.p);
         DL_CHECK_LAUNCH();
-        E.launches++;
     }
-    E.launches++;
     return total;
 }
 
@@ -411,30 +419,30 @@ void merge_rows(Engine& E, const TableView& a, const TableView& b, const TableVi
     const uint64_t total = a.n + b.n;
     if (!total) return;
     const uint64_t threads = (total + kMergeItems - 1) / kMergeItems;
+    KernelScope ks(E, DL_K_MERGE, 8ull * a.arity * total);
     k_merge<<<(unsigned)((threads + kMergeThreads - 1) / kMergeThreads), kMergeThreads, 0, E.stream>>>(a, b, out);
     DL_CHECK_LAUNCH();
-    E.launches++;
 }
 
 void build_root(Engine& E, const uint32_t* col0, uint64_t n, uint32_t* root, uint32_t V) {
     const uint64_t cnt = (uint64_t)V + 1;
+    KernelScope ks(E, DL_K_OTHER, 4 * cnt);
     k_build_root<<<(unsigned)((cnt + 255) / 256), 256, 0, E.stream>>>(col0, (uint32_t)n, root, V);
     DL_CHECK_LAUNCH();
-    E.launches++;
 }
 
 void column_max(Engine& E, const uint32_t* col, uint64_t n, uint32_t* out_dev) {
     if (!n) return;
+    KernelScope ks(E, DL_K_OTHER, 4 * n);
     k_column_max<<<grid_for(n, 256), 256, 0, E.stream>>>(col, n, out_dev);
     DL_CHECK_LAUNCH();
-    E.launches++;
 }
 
 void table_digest(Engine& E, const TableView& t, unsigned long long* d) {
     if (!t.n) return;
+    KernelScope ks(E, DL_K_OTHER, 4ull * t.arity * t.n);
     k_digest<<<grid_for(t.n, 256), 256, 0, E.stream>>>(t, d);
     DL_CHECK_LAUNCH();
-    E.launches++;
 }
 
 void permute_copy(Engine& E, const TableView& in, const uint8_t* perm, const TableView& out) {
@@ -448,9 +456,11 @@ uint64_t count_order_violations(Engine& E, const TableView& t) {
     if (t.n < 2) return 0;
     auto c = E.array<uint64_t>(1);
     DL_CUDA(cudaMemsetAsync(c.p, 0, 8, E.stream));
-    k_order_violations<<<grid_for(t.n, 256), 256, 0, E.stream>>>(t, (unsigned long long*)c.p);
-    DL_CHECK_LAUNCH();
-    E.launches++;
+    {
+        KernelScope ks(E, DL_K_OTHER, 4ull * t.arity * t.n);
+        k_order_violations<<<grid_for(t.n, 256), 256, 0, E.stream>>>(t, (unsigned long long*)c.p);
+        DL_CHECK_LAUNCH();
+    }
     return E.readback(c.p, 1)[0];
 }
 

@@ -438,10 +438,16 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
         auto drv = E.array<uint8_t>(nF);
         P.C = (unsigned long long*)C.p;
         P.drv = drv.p;
+        // algorithmic bytes of one frontier entry read (values + carried ranges)
+        uint32_t nslots_in = 0;
+        for (uint32_t a = 0; a < plan.natoms; a++) nslots_in += slot_of[a] >= 0;
+        const uint64_t entry_bytes = 4ull * (lvl + 2 * nslots_in);
         E.phase_begin(0);
-        k_wcoj_hist<<<(unsigned)((nF + 255) / 256), 256, 0, E.stream>>>(P);
-        DL_CHECK_LAUNCH();
-        E.launches++;
+        {
+            KernelScope ks(E, DL_K_JOIN_HIST, (entry_bytes + 9) * nF);
+            k_wcoj_hist<<<(unsigned)((nF + 255) / 256), 256, 0, E.stream>>>(P);
+            DL_CHECK_LAUNCH();
+        }
         scan_u64(E, C.p, nF, true, C.p + nF);
         const uint64_t T = E.readback(C.p + nF, 1)[0];
         if (T == 0) { E.phase_end(0); return; }
@@ -456,9 +462,11 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
             DL_CUDA(cudaMemsetAsync(dg.p, 0, 24, E.stream));
             P.mode = MODE_COUNT;
             P.digest = (unsigned long long*)dg.p;
-            k_wcoj_count<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
-            DL_CHECK_LAUNCH();
-            E.launches++;
+            {
+                KernelScope ks(E, DL_K_JOIN_COUNT, 4 * T + (entry_bytes + 9) * nF);
+                k_wcoj_count<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+                DL_CHECK_LAUNCH();
+            }
             const uint64_t* d = E.readback(dg.p, 3);
             head.sink_count += d[0];
             head.sink_digest[0] += d[1];
@@ -470,9 +478,11 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
 
         // Phase 2: count -> exclusive offsets
         P.mode = last ? MODE_HEAD : MODE_FRONTIER;
-        k_wcoj_count<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
-        DL_CHECK_LAUNCH();
-        E.launches++;
+        {
+            KernelScope ks(E, DL_K_JOIN_COUNT, 4 * T + (entry_bytes + 9) * nF);
+            k_wcoj_count<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+            DL_CHECK_LAUNCH();
+        }
         scan_u64(E, bc.p, ntiles, false, bc.p + ntiles);
         const uint64_t total = E.readback(bc.p + ntiles, 1)[0];
         if (total == 0) { E.phase_end(0); return; }
@@ -489,9 +499,11 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
                 tv.col[c] = (uint32_t*)buf->ptr + (size_t)c * total;
                 P.ocol[c] = tv.col[c];
             }
-            k_wcoj_write<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
-            DL_CHECK_LAUNCH();
-            E.launches++;
+            {
+                KernelScope ks(E, DL_K_JOIN_WRITE, 4 * T + (entry_bytes + 9) * nF + 4ull * R.head.arity * total);
+                k_wcoj_write<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+                DL_CHECK_LAUNCH();
+            }
             out.parts.push_back(tv);
             out.owners.push_back(buf);
             E.join_rows += total;
@@ -505,9 +517,12 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
             P.olo[c] = (uint32_t*)rng->ptr + (size_t)(2 * c) * total;
             P.ohi[c] = (uint32_t*)rng->ptr + (size_t)(2 * c + 1) * total;
         }
-        k_wcoj_write<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
-        DL_CHECK_LAUNCH();
-        E.launches++;
+        {
+            KernelScope ks(E, DL_K_JOIN_WRITE,
+                           4 * T + (entry_bytes + 9) * nF + 4ull * (lvl + 1 + 2 * P.ncarry) * total);
+            k_wcoj_write<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+            DL_CHECK_LAUNCH();
+        }
         E.phase_end(0);
         // the new frontier
         nF = total;

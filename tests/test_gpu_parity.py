@@ -194,7 +194,13 @@ def test_errors_are_reported_not_raised_across_the_abi():
         eng.relation("E", 2)
         eng.relation("R", 2)
         with pytest.raises(pkg.DatalogError) as ex:
-            eng.rule(("R", ["x", "y"]), [("E", ["x", 3])], ["x"])
+            eng.rule(("R", ["x", "x"]), [("E", ["x", 3])], ["x"])
+        assert ex.value.code == pkg.DL_ERR_UNSUPPORTED
+        with pytest.raises(pkg.DatalogError) as ex:
+            eng.rule(("R", ["x", "y"]), [("E", ["x", "x"])], ["x"])
+        assert ex.value.code == pkg.DL_ERR_ARG
+        with pytest.raises(pkg.DatalogError) as ex:
+            eng.rule(("R", ["x", "x"]), [("E", ["x", "x"])], ["x"])
         assert ex.value.code == pkg.DL_ERR_UNSUPPORTED
         with pytest.raises(pkg.DatalogError) as ex:
             eng.rule(("R", ["x", "y"]), [("E", ["x", "y"])], ["x"])
