@@ -249,6 +249,41 @@ int dl_partition_slices(const uint64_t* C, uint64_t K, uint32_t p, uint64_t* fir
 int dl_decode_unit(const uint64_t* C, const uint64_t* d2, uint64_t K, uint64_t g, uint64_t* key,
                    uint64_t* i1, uint64_t* i2);
 
+/* ------------------------------------------------- allocation-free sort + dedup */
+
+/* The paper has no counterpart to this call.  It serves callers that must not allocate
+ * device memory while they run: for example a plugin inside a host application whose own
+ * allocator owns the whole device budget (an extra cudaMalloc would fail or fragment it), or
+ * a latency-bound service loop where cudaMalloc/cudaFree are banned because they can stall
+ * or synchronise the device.  Such callers cannot create an engine per request, so this
+ * call performs the library's sort + deduplicate step on their own buffers instead.
+ *
+ * It reads nrows rows from the DEVICE columns dcols_in[0..arity) (a host array of device
+ * pointers, one column each) and writes the distinct rows, sorted ascending
+ * lexicographically over columns 0..arity-1 (unsigned), to the DEVICE columns
+ * dcols_out[0..arity), each of which must hold nrows values; *nrows_out (host) receives the
+ * number of distinct rows.  The result equals what dl_load_facts_device followed by
+ * dl_fetch_device returns for an empty relation of that arity.  Inputs are not modified.
+ * Work is issued on `stream` (a cudaStream_t; NULL = the default stream) and the call
+ * synchronises that stream before returning.
+ *
+ * Memory: no allocation at all.  Scratch is one fixed static device array of about 8.1 MiB
+ * (two DL_NOALLOC_MAX_ARITY x DL_NOALLOC_MAX_ROWS uint32 buffers plus counters), which every
+ * GPU that loads the library's device code holds until the process exits.
+ * Limits: arity 1..DL_NOALLOC_MAX_ARITY, nrows <= DL_NOALLOC_MAX_ROWS; larger inputs are
+ * rejected with DL_ERR_CAPACITY before any work is issued.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture begins.
+ * Sharing: all calls on a device use the same array, which keeps the previous call's
+ * contents (every counter the call reads is rewritten by the call first).  Calls whose
+ * work overlaps on the GPU -- on different streams or threads without ordering between
+ * them -- race on the array and corrupt each other's results; order such calls.
+ * Errors: DL_ERR_ARG (NULL pointers, arity 0), DL_ERR_CAPACITY (limits above), DL_ERR_CUDA. */
+#define DL_NOALLOC_MAX_ROWS 262144u
+#define DL_NOALLOC_MAX_ARITY 4u
+int dl_sort_unique_noalloc(const uint32_t* const* dcols_in, uint32_t arity, uint64_t nrows,
+                           uint32_t* const* dcols_out, uint64_t* nrows_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,8 @@ _SIGS = {
     "dl_fetch_digest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p]),
     "dl_partition_slices": (ctypes.c_int, [_u64p, ctypes.c_uint64, ctypes.c_uint32, _u64p, _u64p]),
     "dl_decode_unit": (ctypes.c_int, [_u64p, _u64p, ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p, _u64p]),
+    "dl_sort_unique_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32, ctypes.c_uint64,
+                                              ctypes.POINTER(ctypes.c_void_p), _u64p, ctypes.c_void_p]),
 }
 
 
