@@ -45,7 +45,7 @@ extern "C" {
 /* ------------------------------------------------------------------ limits */
 #define DL_MAX_ARITY 8        /* columns per relation */
 #define DL_MAX_VARS 12        /* distinct variables per rule */
-#define DL_MAX_BODY 8         /* atoms per rule body */
+#define DL_MAX_BODY 12        /* atoms per rule body; at most 8 of them may mention one variable */
 #define DL_MAX_STRATA 64      /* strata reported in dl_stats (more may exist) */
 
 /* dl_config.flags */

@@ -16,6 +16,7 @@ namespace dl {
 constexpr int kMaxArity = DL_MAX_ARITY;
 constexpr int kMaxVars = DL_MAX_VARS;
 constexpr int kMaxAtoms = DL_MAX_BODY;
+constexpr int kMaxSrc = 8;   // atoms that mention one variable (sources of one join level)
 constexpr uint32_t kDenseRootLimit = 1u << 27;  // dense root offsets only below this domain size
 
 // ---------------------------------------------------------------- errors
@@ -153,7 +154,7 @@ struct Stream;  // fwd
 // Exclusive (or inclusive) scan of n uint64 values in place; returns the total through
 // *total_dev (device pointer, may be null).  tmp allocated from the engine.
 void scan_u64(Engine& E, uint64_t* data, uint64_t n, bool inclusive, uint64_t* total_dev);
-void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev);
+void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev, bool inclusive = false);
 
 // Sort the rows of t (arity columns, n rows) lexicographically, col[0] most significant.
 // tmp must have the same shape; on return t holds the sorted rows (buffers may be swapped).

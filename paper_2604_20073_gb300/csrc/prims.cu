@@ -344,8 +344,8 @@ void scan_u64(Engine& E, uint64_t* data, uint64_t n, bool inclusive, uint64_t* t
     scan_impl<unsigned long long>(E, (unsigned long long*)data, n, inclusive, total_dev);
 }
 
-void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev) {
-    scan_impl<uint32_t>(E, data, n, false, total_dev);
+void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev, bool inclusive) {
+    scan_impl<uint32_t>(E, data, n, inclusive, total_dev);
 }
 
 void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out) {

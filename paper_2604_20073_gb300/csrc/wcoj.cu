@@ -23,6 +23,11 @@
 //    Phases 2 and 3): survivors are ranked inside each CTA with a block scan and written in
 //    unit order at the scanned offsets, without atomics.  Unit order is lexicographic
 //    prefix order, so outputs come out sorted by the variable order.
+//  * Candidate reuse: when the sources of level i+1 include an exact copy of level i's
+//    sources (same index, same depth, same bound prefix; e.g. E(w,.) and E(x,.) of the
+//    4-clique), their intersection for a prefix equals level i's surviving candidates for
+//    that prefix, i.e. the values of the entry's siblings in the frontier.  Level i+1 then
+//    reads that sibling run as one already-intersected source instead of re-intersecting.
 #include <algorithm>
 
 #include "engine.h"
@@ -33,6 +38,7 @@ namespace {
 
 constexpr int kJoinThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr uint8_t kVirtual = 0xff;   // source = the entry's sibling run in the frontier
 
 enum { MODE_FRONTIER = 0, MODE_HEAD = 1, MODE_COUNT = 2 };
 
@@ -40,14 +46,17 @@ struct LevelParams {
     AtomView atom[kMaxAtoms];
     uint32_t level;                       // values fval[0..level) are bound by the frontier
     uint32_t nsrc;
-    uint8_t src_atom[kMaxAtoms];
-    uint8_t src_depth[kMaxAtoms];
-    uint8_t src_need_range[kMaxAtoms];    // 1: the narrowed range is carried to the next level
+    uint8_t src_atom[kMaxSrc + 1];        // atom of each source, kVirtual for the sibling run
+    uint8_t src_depth[kMaxSrc + 1];
+    uint8_t src_need_range[kMaxSrc + 1];  // 1: the narrowed range is carried to the next level
     int8_t slot_in[kMaxAtoms];            // frontier slot of each atom's range, -1 = whole index
+    int8_t lazy_pos[kMaxAtoms];           // atom whose depth-0 check was deferred: position of that value
     uint64_t nF;
     const uint32_t* fval[kMaxVars];
     const uint32_t* flo[kMaxAtoms];
     const uint32_t* fhi[kMaxAtoms];
+    const uint32_t* seg;                  // sibling run of each entry: inclusive segment number
+    const uint32_t* segstart;             // first entry of each segment (+ end sentinel)
     unsigned long long* C;                // per entry: W, then inclusive prefix
     uint8_t* drv;                         // per entry: driving source
     uint64_t T;
@@ -56,6 +65,7 @@ struct LevelParams {
     unsigned long long* block_count;      // count pass: per-tile counts; write pass: exclusive offsets
     int mode;
     uint32_t* oval[kMaxVars];
+    uint32_t* oparent;                    // frontier out: parent entry (when the next level reuses)
     uint32_t ncarry;
     int8_t carry_src[kMaxAtoms];          // source index providing the range, or -1
     int8_t carry_slot[kMaxAtoms];         // otherwise: input slot (-1 = whole index)
@@ -69,6 +79,34 @@ struct LevelParams {
     unsigned long long* digest;           // MODE_COUNT: [count, sum, xor]
 };
 
+// Row range of source s for frontier entry e, and the column its candidates live in.
+__device__ __forceinline__ const uint32_t* src_range(const LevelParams& P, int s, uint64_t e, uint32_t& lo,
+                                                     uint32_t& hi) {
+    const int a = P.src_atom[s];
+    if (a == kVirtual) {
+        const uint32_t g = __ldg(P.seg + e) - 1;
+        lo = __ldg(P.segstart + g);
+        hi = __ldg(P.segstart + g + 1);
+        return P.fval[P.level - 1];
+    }
+    const int d = P.src_depth[s];
+    if (d == 0) {
+        lo = 0;
+        hi = P.atom[a].n;
+    } else if (P.slot_in[a] >= 0) {
+        const int slot = P.slot_in[a];
+        lo = __ldg(P.flo[slot] + e);
+        hi = __ldg(P.fhi[slot] + e);
+    } else {
+        // the atom's depth-0 value was bound earlier with its check deferred: narrow now
+        const uint32_t v0 = __ldg(P.fval[P.lazy_pos[a]] + e);
+        lo = 0;
+        hi = P.atom[a].n;
+        if (!narrow(P.atom[a], 0, v0, lo, hi)) lo = hi = 0;
+    }
+    return P.atom[a].col[d];
+}
+
 __global__ void k_wcoj_hist(const __grid_constant__ LevelParams P) {
     const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (e >= P.nF) return;
@@ -76,13 +114,14 @@ __global__ void k_wcoj_hist(const __grid_constant__ LevelParams P) {
     uint32_t bs = 0;
     for (uint32_t s = 0; s < P.nsrc; s++) {
         const int a = P.src_atom[s], d = P.src_depth[s];
-        const AtomView& A = P.atom[a];
         unsigned long long len;
-        if (d == 0) {
+        if (a != kVirtual && d == 0) {
+            const AtomView& A = P.atom[a];
             len = A.n == 0 ? 0 : (A.root ? A.V : A.n);
         } else {
-            const int slot = P.slot_in[a];
-            len = P.fhi[slot][e] - P.flo[slot][e];
+            uint32_t lo, hi;
+            src_range(P, (int)s, e, lo, hi);
+            len = hi - lo;
         }
         if (len < best) { best = len; bs = s; }
     }
@@ -93,58 +132,54 @@ __global__ void k_wcoj_hist(const __grid_constant__ LevelParams P) {
 struct Unit {
     uint64_t e;
     uint32_t v;
-    uint32_t lo[kMaxAtoms], hi[kMaxAtoms];
+    uint32_t lo[kMaxSrc + 1], hi[kMaxSrc + 1];
 };
 
 // Decode unit u of the flat space into (entry, local) and evaluate it.
 __device__ __forceinline__ bool eval_unit(const LevelParams& P, uint64_t u, uint64_t e0, uint64_t e1, Unit& U) {
-    uint64_t e, local;
-    if (P.naive) {
-        e = e0;
-        local = u - (e ? P.C[e - 1] : 0);
-    } else {
-        e = upper_bound_u64((const uint64_t*)P.C, e0, e1, u);
-        local = u - (e ? P.C[e - 1] : 0);
-    }
+    uint64_t e;
+    if (P.naive) e = e0;
+    else e = upper_bound_u64((const uint64_t*)P.C, e0, e1, u);
+    const uint64_t local = u - (e ? P.C[e - 1] : 0);
     U.e = e;
     const int s0 = P.drv[e];
-    uint32_t v;
+    uint32_t v, d_lo, d_hi;   // the driving source's narrowed range for v
     {
         const int a = P.src_atom[s0], d = P.src_depth[s0];
-        const AtomView& A = P.atom[a];
-        if (d == 0 && A.root) {
+        if (a != kVirtual && d == 0 && P.atom[a].root) {
+            const AtomView& A = P.atom[a];
             v = (uint32_t)local;                       // iterate the dense value domain
-            if (__ldg(A.root + v) >= __ldg(A.root + v + 1)) return false;
+            d_lo = __ldg(A.root + v);
+            d_hi = __ldg(A.root + v + 1);
+            if (d_lo >= d_hi) return false;
         } else {
-            uint32_t lo = 0;
-            if (d != 0) lo = P.flo[P.slot_in[a]][e];
+            uint32_t lo, hi;
+            const uint32_t* col = src_range(P, s0, e, lo, hi);
             const uint32_t r = lo + (uint32_t)local;
-            const uint32_t* col = A.col[d];
             v = __ldg(col + r);
             if (r > lo && __ldg(col + r - 1) == v) return false;   // not the first row of its value
+            d_lo = r;
+            d_hi = P.src_need_range[s0] ? upper_bound_u32(col, r + 1, hi, v) : r + 1;
         }
     }
     U.v = v;
 #pragma unroll
-    for (int s = 0; s < kMaxAtoms; s++) {
+    for (int s = 0; s < kMaxSrc + 1; s++) {
         if (s >= (int)P.nsrc) break;
-        const int a = P.src_atom[s], d = P.src_depth[s];
-        const AtomView& A = P.atom[a];
-        uint32_t lo, hi;
-        if (d == 0) {
-            lo = 0;
-            hi = A.n;
-        } else {
-            const int slot = P.slot_in[a];
-            lo = P.flo[slot][e];
-            hi = P.fhi[slot][e];
+        if (s == s0) {               // the driver holds v by construction
+            U.lo[s] = d_lo;
+            U.hi[s] = d_hi;
+            continue;
         }
+        const int a = P.src_atom[s], d = P.src_depth[s];
+        uint32_t lo, hi;
+        const uint32_t* col = src_range(P, s, e, lo, hi);
         if (P.src_need_range[s]) {
-            if (!narrow(A, d, v, lo, hi)) return false;
-        } else if (d == 0 && A.root) {
+            if (!narrow(P.atom[a], d, v, lo, hi)) return false;
+        } else if (a != kVirtual && d == 0 && P.atom[a].root) {
+            const AtomView& A = P.atom[a];
             if (v >= A.V || __ldg(A.root + v) >= __ldg(A.root + v + 1)) return false;
         } else {
-            const uint32_t* col = A.col[d];
             const uint32_t l = lower_bound_u32(col, lo, hi, v);
             if (l >= hi || __ldg(col + l) != v) return false;
         }
@@ -186,10 +221,9 @@ __device__ __forceinline__ T block_sum(T v) {
     return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kJoinThreads) k_wcoj_count(const __grid_constant__ LevelParams P) {
+__device__ __forceinline__ void tile_entries(const LevelParams& P, uint64_t tlo, uint64_t thi, uint64_t& e0,
+                                             uint64_t& e1) {
     __shared__ uint64_t s_e0, s_e1;
-    uint64_t tlo, thi;
-    tile_bounds(P, tlo, thi);
     if (threadIdx.x == 0) {
         if (P.naive) {
             s_e0 = blockIdx.x;
@@ -197,10 +231,19 @@ __global__ void __launch_bounds__(kJoinThreads) k_wcoj_count(const __grid_consta
         } else if (tlo < thi) {
             s_e0 = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, tlo);
             s_e1 = upper_bound_u64((const uint64_t*)P.C, s_e0, P.nF, thi - 1) + 1;
+        } else {
+            s_e0 = s_e1 = 0;
         }
     }
     __syncthreads();
-    const uint64_t e0 = s_e0, e1 = s_e1;
+    e0 = s_e0;
+    e1 = s_e1;
+}
+
+__global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_count(const __grid_constant__ LevelParams P) {
+    uint64_t tlo, thi, e0, e1;
+    tile_bounds(P, tlo, thi);
+    tile_entries(P, tlo, thi, e0, e1);
     unsigned long long cnt = 0, hs = 0, hx = 0;
     Unit U;
     for (uint64_t u = tlo + threadIdx.x; u < thi; u += blockDim.x) {
@@ -257,21 +300,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_
     return pre + x - v;
 }
 
-__global__ void __launch_bounds__(kJoinThreads) k_wcoj_write(const __grid_constant__ LevelParams P) {
-    __shared__ uint64_t s_e0, s_e1;
-    uint64_t tlo, thi;
+__global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_write(const __grid_constant__ LevelParams P) {
+    uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
-    if (threadIdx.x == 0) {
-        if (P.naive) {
-            s_e0 = blockIdx.x;
-            s_e1 = blockIdx.x + 1;
-        } else if (tlo < thi) {
-            s_e0 = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, tlo);
-            s_e1 = upper_bound_u64((const uint64_t*)P.C, s_e0, P.nF, thi - 1) + 1;
-        }
-    }
-    __syncthreads();
-    const uint64_t e0 = s_e0, e1 = s_e1;
+    tile_entries(P, tlo, thi, e0, e1);
     uint64_t run = P.block_count[blockIdx.x];
     Unit U;
     for (uint64_t base = tlo; base < thi; base += blockDim.x) {
@@ -288,6 +320,7 @@ __global__ void __launch_bounds__(kJoinThreads) k_wcoj_write(const __grid_consta
                 }
             } else {
                 for (uint32_t k = 0; k <= P.level; k++) P.oval[k][o] = value_at(P, U, (int)k);
+                if (P.oparent) P.oparent[o] = (uint32_t)U.e;
 #pragma unroll
                 for (int c = 0; c < kMaxAtoms; c++) {
                     if (c >= (int)P.ncarry) break;
@@ -295,9 +328,10 @@ __global__ void __launch_bounds__(kJoinThreads) k_wcoj_write(const __grid_consta
                     uint32_t lo, hi;
                     if (s >= 0) {
                         // registers hold the ranges by source index; select without local arrays
-                        lo = 0; hi = 0;
+                        lo = 0;
+                        hi = 0;
 #pragma unroll
-                        for (int q = 0; q < kMaxAtoms; q++)
+                        for (int q = 0; q < kMaxSrc + 1; q++)
                             if (q == s) { lo = U.lo[q]; hi = U.hi[q]; }
                     } else if (P.carry_slot[c] >= 0) {
                         lo = __ldg(P.flo[P.carry_slot[c]] + U.e);
@@ -315,16 +349,41 @@ __global__ void __launch_bounds__(kJoinThreads) k_wcoj_write(const __grid_consta
     }
 }
 
+// Sibling runs of a frontier: seg[k] = 1 if entry k starts a new parent's run.
+__global__ void k_seg_flags(const uint32_t* __restrict__ parent, uint64_t n, uint32_t* __restrict__ seg) {
+    const uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (k < n) seg[k] = (k == 0 || parent[k] != parent[k - 1]) ? 1u : 0u;
+}
+
+// After an inclusive scan seg[k] is the 1-based run number; record each run's first entry.
+__global__ void k_seg_starts(const uint32_t* __restrict__ parent, const uint32_t* __restrict__ seg, uint64_t n,
+                             uint32_t* __restrict__ segstart) {
+    const uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (k == 0 || parent[k] != parent[k - 1]) segstart[seg[k] - 1] = (uint32_t)k;
+    if (k == n - 1) segstart[seg[k]] = (uint32_t)n;
+}
+
 // ---------------------------------------------------------------- host plan
+
+struct Src {
+    int atom;
+    int depth;
+};
 
 struct Plan {
     uint32_t m = 0, natoms = 0;
     uint8_t colpos[kMaxAtoms][kMaxArity];   // order position held by index column k of atom a
     uint8_t arity[kMaxAtoms];
     int first_level[kMaxAtoms], last_level[kMaxAtoms];
+    int touch_level[kMaxAtoms];             // level whose pass first narrows the atom's range
+    int lazy_pos[kMaxAtoms];                // deferred depth-0 check: the value's position, else -1
+    std::vector<std::vector<Src>> src;      // per level: the atoms binding the level's variable
+    std::vector<uint32_t> reuse_mask;       // per level: atoms replaced by the previous level's siblings
+    std::vector<uint32_t> defer_mask;       // per level: atoms whose depth-0 check moves to their next level
 };
 
-Plan make_plan(const Rule& R) {
+Plan make_plan(const Rule& R, const std::vector<const Index*>& idx) {
     Plan p;
     p.m = (uint32_t)R.order.size();
     p.natoms = (uint32_t)R.body.size();
@@ -339,7 +398,72 @@ Plan make_plan(const Rule& R) {
         p.first_level[a] = pos.front();
         p.last_level[a] = pos.back();
     }
+    p.src.resize(p.m);
+    p.reuse_mask.assign(p.m, 0);
+    p.defer_mask.assign(p.m, 0);
+    for (uint32_t l = 0; l < p.m; l++)
+        for (uint32_t a = 0; a < p.natoms; a++)
+            for (uint32_t k = 0; k < p.arity[a]; k++)
+                if (p.colpos[a][k] == l) p.src[l].push_back({(int)a, (int)k});
+    // Candidate reuse at level l: every source applied at level l-1 has a twin among level
+    // l's sources (same index, same depth, same bound prefix) whose atom has no variable after
+    // level l; then the intersection of those twins, for an entry's prefix, is exactly the set
+    // of the entry's siblings.  A depth-0 source at level l-1 whose atom has a later variable
+    // may be left out of level l-1 (its check "the value occurs in column 0" is made at the
+    // atom's next level instead, where its range is narrowed anyway) when that is what makes
+    // the match possible.  Reuse is only taken when it replaces an intersection of >= 2
+    // sources.
+    for (uint32_t l = 1; l < p.m; l++) {
+        uint32_t defer = 0;
+        std::vector<Src> applied;
+        for (const Src& b : p.src[l - 1]) {
+            if (b.depth == 0 && p.last_level[b.atom] > (int)l - 1) defer |= 1u << b.atom;
+            else applied.push_back(b);
+        }
+        if (applied.size() < 2) continue;
+        uint32_t used = 0;
+        bool ok = true;
+        for (const Src& b : applied) {
+            bool found = false;
+            for (const Src& a : p.src[l]) {
+                if ((used >> a.atom) & 1u) continue;
+                if (idx[a.atom] != idx[b.atom] || a.depth != b.depth || p.last_level[a.atom] != (int)l) continue;
+                bool same = true;
+                for (int k = 0; k < a.depth && same; k++) same = p.colpos[a.atom][k] == p.colpos[b.atom][k];
+                if (!same) continue;
+                used |= 1u << a.atom;
+                found = true;
+                break;
+            }
+            if (!found) { ok = false; break; }
+        }
+        if (ok) {
+            p.reuse_mask[l] = used;
+            p.defer_mask[l - 1] = defer;
+        }
+    }
+    for (uint32_t a = 0; a < p.natoms; a++) {
+        p.touch_level[a] = p.first_level[a];
+        p.lazy_pos[a] = -1;
+        if ((p.defer_mask[p.first_level[a]] >> a) & 1u) {
+            p.lazy_pos[a] = p.first_level[a];
+            p.touch_level[a] = p.colpos[a][1];
+        }
+    }
     return p;
+}
+
+void launch_seg(Engine& E, const uint32_t* parent, uint64_t n, uint32_t* seg, uint32_t* segstart) {
+    const unsigned g = (unsigned)((n + 255) / 256);
+    {
+        KernelScope ks(E, DL_K_OTHER, 12 * n);
+        k_seg_flags<<<g, 256, 0, E.stream>>>(parent, n, seg);
+        DL_CHECK_LAUNCH();
+    }
+    scan_u32(E, seg, n, nullptr, true);
+    KernelScope ks(E, DL_K_OTHER, 16 * n);
+    k_seg_starts<<<g, 256, 0, E.stream>>>(parent, seg, n, segstart);
+    DL_CHECK_LAUNCH();
 }
 
 }  // namespace
@@ -366,7 +490,7 @@ bool head_is_order(const Rule& R) {
 }
 
 void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Relation& head, JoinOutput& out) {
-    const Plan plan = make_plan(R);
+    const Plan plan = make_plan(R, src);
     const bool count_sink = head.sink == DL_SINK_COUNT;
     out.sorted_unique = head_is_order(R);
 
@@ -390,16 +514,22 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
 
     // frontier state (host handles)
     uint64_t nF = 1;
-    std::vector<DevPtr> f_vals_owner, f_rng_owner;
+    DevPtr f_vals_owner, f_rng_owner, f_seg_owner;
     const uint32_t* f_vals[kMaxVars] = {nullptr};
     const uint32_t* f_lo[kMaxAtoms] = {nullptr};
     const uint32_t* f_hi[kMaxAtoms] = {nullptr};
+    const uint32_t* f_seg = nullptr;
+    const uint32_t* f_segstart = nullptr;
     int8_t slot_of[kMaxAtoms];
     for (int a = 0; a < kMaxAtoms; a++) slot_of[a] = -1;
+    for (uint32_t a = 0; a < plan.natoms; a++) P.lazy_pos[a] = (int8_t)plan.lazy_pos[a];
 
     auto C = E.array<uint64_t>(1);
     for (uint32_t lvl = 0; lvl < plan.m; lvl++) {
         const bool last = lvl + 1 == plan.m;
+        const uint32_t reuse = plan.reuse_mask[lvl];
+        const uint32_t defer = plan.defer_mask[lvl];
+        const uint32_t next_reuse = last ? 0 : plan.reuse_mask[lvl + 1];
         P.level = lvl;
         P.nF = nF;
         for (uint32_t k = 0; k < lvl; k++) P.fval[k] = f_vals[k];
@@ -410,21 +540,31 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
                 P.fhi[slot_of[a]] = f_hi[slot_of[a]];
             }
         }
-        // sources of this level
+        P.seg = f_seg;
+        P.segstart = f_segstart;
+        // sources of this level (atoms covered by candidate reuse become one sibling source)
         P.nsrc = 0;
-        for (uint32_t a = 0; a < plan.natoms; a++)
-            for (uint32_t k = 0; k < plan.arity[a]; k++)
-                if (plan.colpos[a][k] == lvl) {
-                    P.src_atom[P.nsrc] = (uint8_t)a;
-                    P.src_depth[P.nsrc] = (uint8_t)k;
-                    P.src_need_range[P.nsrc] = plan.last_level[a] > (int)lvl ? 1 : 0;
-                    P.nsrc++;
-                }
-        // carried atoms: touched at or before this level and still needed later
+        for (const Src& s : plan.src[lvl]) {
+            if (((reuse | defer) >> s.atom) & 1u) continue;
+            P.src_atom[P.nsrc] = (uint8_t)s.atom;
+            P.src_depth[P.nsrc] = (uint8_t)s.depth;
+            P.src_need_range[P.nsrc] = plan.last_level[s.atom] > (int)lvl ? 1 : 0;
+            P.nsrc++;
+        }
+        if (P.nsrc > (uint32_t)kMaxSrc)
+            throw Error(DL_ERR_UNSUPPORTED, "more than 8 body atoms mention one variable");
+        if (reuse) {
+            P.src_atom[P.nsrc] = kVirtual;
+            P.src_depth[P.nsrc] = 0;
+            P.src_need_range[P.nsrc] = 0;
+            P.nsrc++;
+        }
+        // carried atoms: touched at or before this level and still needed later (atoms the
+        // next level replaces by its sibling source are not needed)
         P.ncarry = 0;
         if (!last)
             for (uint32_t a = 0; a < plan.natoms; a++)
-                if (plan.first_level[a] <= (int)lvl && plan.last_level[a] > (int)lvl) {
+                if (plan.touch_level[a] <= (int)lvl && plan.last_level[a] > (int)lvl && !((next_reuse >> a) & 1u)) {
                     const int c = (int)P.ncarry++;
                     P.carry_atom[c] = (uint8_t)a;
                     P.carry_src[c] = -1;
@@ -433,15 +573,16 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
                     P.carry_slot[c] = slot_of[a];
                 }
 
+        // algorithmic bytes of one frontier entry read (values + carried ranges + sibling run)
+        uint32_t nslots_in = 0;
+        for (uint32_t a = 0; a < plan.natoms; a++) nslots_in += slot_of[a] >= 0;
+        const uint64_t entry_bytes = 4ull * (lvl + 2 * nslots_in) + (reuse ? 8 : 0);
+
         // Phase 1: histogram + prefix
         C = E.array<uint64_t>(nF + 1);
         auto drv = E.array<uint8_t>(nF);
         P.C = (unsigned long long*)C.p;
         P.drv = drv.p;
-        // algorithmic bytes of one frontier entry read (values + carried ranges)
-        uint32_t nslots_in = 0;
-        for (uint32_t a = 0; a < plan.natoms; a++) nslots_in += slot_of[a] >= 0;
-        const uint64_t entry_bytes = 4ull * (lvl + 2 * nslots_in);
         E.phase_begin(0);
         {
             KernelScope ks(E, DL_K_JOIN_HIST, (entry_bytes + 9) * nF);
@@ -510,18 +651,35 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
             E.phase_end(0);
             return;
         }
+        if (next_reuse && (nF >= (1ull << 32) || total >= (1ull << 32)))
+            throw Error(DL_ERR_CAPACITY, "join frontier of 2^32 entries or more");
         auto vals = E.make(sizeof(uint32_t) * (lvl + 1) * total);
         auto rng = E.make(sizeof(uint32_t) * 2 * std::max<uint32_t>(1, P.ncarry) * total);
+        DevPtr parent, segbuf;
         for (uint32_t k = 0; k <= lvl; k++) P.oval[k] = (uint32_t*)vals->ptr + (size_t)k * total;
         for (uint32_t c = 0; c < P.ncarry; c++) {
             P.olo[c] = (uint32_t*)rng->ptr + (size_t)(2 * c) * total;
             P.ohi[c] = (uint32_t*)rng->ptr + (size_t)(2 * c + 1) * total;
         }
+        P.oparent = nullptr;
+        if (next_reuse) {
+            parent = E.make(sizeof(uint32_t) * total);
+            P.oparent = (uint32_t*)parent->ptr;
+        }
         {
             KernelScope ks(E, DL_K_JOIN_WRITE,
-                           4 * T + (entry_bytes + 9) * nF + 4ull * (lvl + 1 + 2 * P.ncarry) * total);
+                           4 * T + (entry_bytes + 9) * nF + 4ull * (lvl + 1 + 2 * P.ncarry + (next_reuse ? 1 : 0)) * total);
             k_wcoj_write<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
             DL_CHECK_LAUNCH();
+        }
+        f_seg = f_segstart = nullptr;
+        if (next_reuse) {
+            segbuf = E.make(sizeof(uint32_t) * (2 * total + 1));
+            uint32_t* seg = (uint32_t*)segbuf->ptr;
+            uint32_t* segstart = seg + total;
+            launch_seg(E, P.oparent, total, seg, segstart);
+            f_seg = seg;
+            f_segstart = segstart;
         }
         E.phase_end(0);
         // the new frontier
@@ -533,8 +691,9 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
             f_lo[c] = P.olo[c];
             f_hi[c] = P.ohi[c];
         }
-        f_vals_owner.assign(1, vals);
-        f_rng_owner.assign(1, rng);
+        f_vals_owner = vals;
+        f_rng_owner = rng;
+        f_seg_owner = segbuf;
     }
 }
 

@@ -104,6 +104,28 @@ def test_variable_order_does_not_change_results(order):
     check(P.TC_TRI_RELS, {"E": e}, tc + tri)
 
 
+# 5-clique; atoms listed so that the oracle's left-deep plan closes each triangle early
+Q5 = [(("Q5", ["a", "b", "c", "d", "e"]),
+       [("E", [u, v]) for j, v in enumerate("abcde") for u in "abcde"[:j]], ["a", "b", "c", "d", "e"])]
+# same rule on a directed graph, where deferring a depth-0 check changes which prefixes survive
+DQ4 = [(("DQ4", ["w", "x", "y", "z"]), P.Q4[0][1], ["w", "x", "y", "z"])]
+
+
+@pytest.mark.parametrize("order", [["w", "x", "y", "z"], ["x", "w", "z", "y"], ["z", "y", "x", "w"]])
+def test_clique_orders_and_candidate_reuse(order):
+    e = dg.rmat_edges(1 << 8, 3000, 404, symmetric=True)
+    rels = {"E": 2, "Q4": 4, "Q5": 5}
+    q4 = [(P.Q4[0][0], P.Q4[0][1], order)]
+    got = check(rels, {"E": e}, q4 + Q5)[0]
+    assert len(got["Q5"]) > 0 and len(got["Q4"]) > 0
+
+
+def test_directed_cliques_with_deferred_checks():
+    e = dg.rmat_edges(1 << 9, 6000, 405)
+    got = check({"E": 2, "DQ4": 4, "Tri": 3}, {"E": e}, DQ4 + P.TRI)[0]
+    assert len(got["DQ4"]) > 0
+
+
 def test_rerun_is_deterministic_and_debug_checks_pass():
     e = dg.rmat_edges(2048, 16000, 5)
     a = gpu(P.TC_TRI_RELS, {"E": e}, P.TC_TRI, flags=pkg.DL_FLAG_DEBUG_CHECKS)
