@@ -74,7 +74,23 @@ typedef struct dl_config {
     void* alloc_user;
     uint32_t flags;           /* DL_FLAG_* */
     uint32_t tile_units;      /* join work units per CTA tile; 0 = default (4096) */
+    uint32_t instances;       /* 0: one program.  N >= 1: batched form, see below */
+    uint64_t chunk_rows;      /* a rule's raw output per round above this many rows is written and
+                                 reduced (sorted, deduplicated, anti-joined) in chunks of at most
+                                 this size; 0 = default (2^30) */
 } dl_config;
+
+/* Batched form (dl_config.instances = N >= 1).  The engine holds N independent instances
+ * of one program: every relation and rule is declared once, facts are loaded per instance
+ * (dl_load_facts_instance) and results read per instance (dl_fetch_instance,
+ * dl_instance_rounds).  One dl_fixpoint call evaluates all instances together, each
+ * evaluation stage being one launch over all of them (the instance id is an extra leading
+ * join variable shared by every atom, so instances never join with each other and the
+ * work histogram balances uneven instances across the GPU).  Results and per-instance round
+ * counts equal those of evaluating each instance alone.  In this form relations have at
+ * most DL_MAX_ARITY - 1 columns and rules at most DL_MAX_VARS - 1 variables; count sinks,
+ * dl_load_facts*, dl_fetch and dl_fetch_device are not available (DL_ERR_STATE); every
+ * relation, summed over its instances, holds fewer than 2^32 rows. */
 
 /* ------------------------------------------------------------------ engine */
 
@@ -213,7 +229,26 @@ int dl_stratum_info(dl_engine* e, uint32_t s, dl_rel_id* rels, uint32_t cap, uin
 
 /* --------------------------------------------------------------------- fetch */
 
-/* Number of tuples currently in a relation (DL_SINK_COUNT: the counted tuples). */
+/* Batched form: add facts to instance `inst` (< dl_config.instances) of a relation from
+ * HOST column pointers, as dl_load_facts does for a single program.  Loads are merged into
+ * the relation lazily (at the next dl_fixpoint or fetch), so loading many instances costs
+ * one sort and merge in total.  Errors: DL_ERR_ARG (bad id or instance), DL_ERR_STATE (not
+ * a batched engine), DL_ERR_CAPACITY. */
+int dl_load_facts_instance(dl_engine* e, dl_rel_id rel, uint32_t inst, const uint32_t* const* cols,
+                           uint64_t nrows);
+
+/* Batched form: copy instance `inst` of a relation to HOST memory, column-major, rows
+ * distinct and sorted as dl_fetch does; NULL cols_out returns only *nrows_out. */
+int dl_fetch_instance(dl_engine* e, dl_rel_id rel, uint32_t inst, uint32_t* const* cols_out, uint64_t cap_rows,
+                      uint64_t* nrows_out);
+
+/* Batched form, after dl_fixpoint: round count of instance `inst` in each stratum (the
+ * count it would have alone, same definition as dl_stats.rounds) into rounds[0..cap);
+ * *nstrata receives the number of strata. */
+int dl_instance_rounds(dl_engine* e, uint32_t inst, uint32_t* rounds, uint32_t cap, uint32_t* nstrata);
+
+/* Number of tuples currently in a relation (DL_SINK_COUNT: the counted tuples; batched
+ * form: summed over instances). */
 int dl_relation_size(dl_engine* e, dl_rel_id rel, uint64_t* nrows);
 
 /* Copy a relation to HOST memory, column-major: cols_out[j] receives column j.  Rows are

@@ -46,7 +46,8 @@ DL_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_v
 class dl_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
                 ("alloc", DL_ALLOC_FN), ("free", DL_FREE_FN), ("alloc_user", ctypes.c_void_p),
-                ("flags", ctypes.c_uint32), ("tile_units", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("tile_units", ctypes.c_uint32), ("instances", ctypes.c_uint32),
+                ("chunk_rows", ctypes.c_uint64)]
 
 
 class dl_term(ctypes.Structure):
@@ -98,6 +99,11 @@ _SIGS = {
     "dl_fetch_digest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p]),
     "dl_partition_slices": (ctypes.c_int, [_u64p, ctypes.c_uint64, ctypes.c_uint32, _u64p, _u64p]),
     "dl_decode_unit": (ctypes.c_int, [_u64p, _u64p, ctypes.c_uint64, ctypes.c_uint64, _u64p, _u64p, _u64p]),
+    "dl_load_facts_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_u32p),
+                                              ctypes.c_uint64]),
+    "dl_fetch_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_u32p),
+                                         ctypes.c_uint64, _u64p]),
+    "dl_instance_rounds": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p]),
     "dl_sort_unique_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32, ctypes.c_uint64,
                                               ctypes.POINTER(ctypes.c_void_p), _u64p, ctypes.c_void_p]),
 }
@@ -147,7 +153,7 @@ class Engine:
     """One engine handle (owns all of its device memory)."""
 
     def __init__(self, device: int = 0, stream=None, arena_bytes: int = 0, flags: int = 0, tile_units: int = 0,
-                 use_torch_allocator: bool = False):
+                 use_torch_allocator: bool = False, instances: int = 0, chunk_rows: int = 0):
         import torch  # plumbing only: stream handle and (optionally) the caching allocator
         self.lib = load_library()
         if not torch.cuda.is_available():
@@ -162,6 +168,9 @@ class Engine:
         cfg.arena_bytes = arena_bytes
         cfg.flags = flags
         cfg.tile_units = tile_units
+        cfg.instances = instances
+        cfg.chunk_rows = chunk_rows
+        self.instances = instances
         self._cb = None
         if use_torch_allocator:
             def _alloc(nbytes, strm, user):
@@ -225,6 +234,27 @@ class Engine:
         rows = np.asarray(rows, dtype=np.uint32).reshape(-1, self.arity[name])
         cols = [np.ascontiguousarray(rows[:, c]) for c in range(rows.shape[1])]
         self._check(self.lib.dl_load_facts(self.h, self.rel_ids[name], _cols_ptrs(cols), rows.shape[0]))
+
+    def load_instance(self, name: str, inst: int, rows):
+        """Batched form: add (n, arity) uint32 host rows to instance `inst` of a relation."""
+        rows = np.asarray(rows, dtype=np.uint32).reshape(-1, self.arity[name])
+        cols = [np.ascontiguousarray(rows[:, c]) for c in range(rows.shape[1])]
+        self._check(self.lib.dl_load_facts_instance(self.h, self.rel_ids[name], inst, _cols_ptrs(cols), rows.shape[0]))
+
+    def fetch_instance(self, name: str, inst: int) -> np.ndarray:
+        n = ctypes.c_uint64()
+        rid = self.rel_ids[name]
+        self._check(self.lib.dl_fetch_instance(self.h, rid, inst, None, 0, ctypes.byref(n)))
+        a = self.arity[name]
+        cols = [np.empty(n.value, dtype=np.uint32) for _ in range(a)]
+        self._check(self.lib.dl_fetch_instance(self.h, rid, inst, _cols_ptrs(cols), n.value, ctypes.byref(n)))
+        return np.stack(cols, axis=1)
+
+    def instance_rounds(self, inst: int) -> list:
+        r = (ctypes.c_uint32 * DL_MAX_STRATA)()
+        ns = ctypes.c_uint32()
+        self._check(self.lib.dl_instance_rounds(self.h, inst, r, DL_MAX_STRATA, ctypes.byref(ns)))
+        return list(r[: ns.value])
 
     def clear(self, name: str):
         self._check(self.lib.dl_relation_clear(self.h, self.rel_ids[name]))
@@ -321,6 +351,26 @@ def build_program(eng: Engine, relations: dict, rules: list, sinks: dict | None 
         eng.set_sink(name, s)
     for r in rules:
         eng.rule(r[0], r[1], r[2])
+
+
+def run_batched(relations: dict, facts_per_instance: list, rules: list, **cfg):
+    """Evaluate independent instances of one program together (batched form); returns
+    (per-instance relations dicts, per-instance [(stratum relation names, rounds)], stats)."""
+    n = len(facts_per_instance)
+    with Engine(instances=n, **cfg) as eng:
+        build_program(eng, relations, rules)
+        for i, facts in enumerate(facts_per_instance):
+            for name, rows in facts.items():
+                if len(rows):
+                    eng.load_instance(name, i, rows)
+        stats = eng.fixpoint()
+        strata = eng.strata()
+        outs, rounds = [], []
+        for i in range(n):
+            outs.append({name: eng.fetch_instance(name, i) for name in relations})
+            r = eng.instance_rounds(i)
+            rounds.append([(rels, r[k]) for k, (rels, _) in enumerate(strata)])
+        return outs, rounds, stats
 
 
 def run_program(relations: dict, facts: dict, rules: list, sinks: dict | None = None, **cfg):

@@ -237,6 +237,35 @@ void add_rows(Engine& E, Relation& R, DevPtr buf, TableView t) {
     check_sorted(E, R.full[0], R.name);
 }
 
+// Merge every pending load of a relation into its full index (one sort and merge in total).
+void flush_pending(Engine& E, Relation& R) {
+    if (R.pending.empty()) return;
+    if (R.pending.size() == 1) {
+        auto pr = R.pending[0];
+        R.pending.clear();
+        add_rows(E, R, pr.first, pr.second);
+        return;
+    }
+    uint64_t tot = 0;
+    for (auto& pr : R.pending) tot += pr.second.n;
+    if (tot >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "2^32 or more pending rows in one relation");
+    DevPtr buf = E.make(sizeof(uint32_t) * R.arity * tot);
+    TableView t;
+    memset(&t, 0, sizeof(t));
+    t.arity = R.arity;
+    t.n = tot;
+    for (uint32_t c = 0; c < R.arity; c++) t.col[c] = (uint32_t*)buf->ptr + (size_t)c * tot;
+    uint64_t off = 0;
+    for (auto& pr : R.pending) {
+        for (uint32_t c = 0; c < R.arity; c++)
+            DL_CUDA(cudaMemcpyAsync(t.col[c] + off, pr.second.col[c], sizeof(uint32_t) * pr.second.n,
+                                    cudaMemcpyDeviceToDevice, E.stream));
+        off += pr.second.n;
+    }
+    R.pending.clear();
+    add_rows(E, R, buf, t);
+}
+
 void update_max_value(Engine& E, const TableView& t) {
     if (!t.n) return;
     auto m = E.array<uint32_t>(2);
@@ -357,13 +386,48 @@ struct PendingOut {
     uint32_t producers = 0;   // variants that produced parts
 };
 
+// a ∪ b of two sorted, duplicate-free indexes (rows may occur in both).
+Index union_sorted(Engine& E, const Index& a, const Index& b) {
+    if (a.n == 0) return b;
+    if (b.n == 0) return a;
+    Perm p = identity_perm();
+    for (int k = 0; k < kMaxArity; k++) p[k] = a.perm[k];
+    Index m = make_index(E, a.arity, p, a.n + b.n);
+    E.phase_begin(3);
+    merge_rows(E, table_of(a), table_of(b), table_of(m));
+    E.phase_end(3);
+    Index u = make_index(E, a.arity, p, m.n);
+    E.phase_begin(2);
+    u.n = unique_anti(E, table_of(m), nullptr, table_of(u));
+    E.phase_end(2);
+    return u;
+}
+
+// Sort a raw output part, drop duplicates and rows already in full.
+Index reduce_part(Engine& E, Relation& R, DevPtr buf, TableView t) {
+    Index sorted = sort_into_index(E, buf, t, identity_perm(), R.arity);
+    return compute_delta(E, sorted, R.full[0], identity_perm(), R.arity, false);
+}
+
 // Turn one round's join outputs for relation R into its new delta; merge into full.
 // Returns |Δ|.
 uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
     JoinOutput& jo = P.out;
     Index newrows = empty_index(R.arity, identity_perm());
     bool known_unique = false;
-    if (jo.parts.size() == 1 && jo.sorted_unique) {
+    uint64_t raw = 0;
+    for (auto& p : jo.parts) raw += p.n;
+    Index d;
+    if (!jo.rparts.empty() || raw > E.chunk_rows) {
+        // reduce every part on its own, then union (memory stays proportional to new tuples)
+        Index acc = empty_index(R.arity, identity_perm());
+        for (size_t i = 0; i < jo.parts.size(); i++) acc = union_sorted(E, acc, reduce_part(E, R, jo.owners[i], jo.parts[i]));
+        jo.parts.clear();
+        jo.owners.clear();
+        for (Index& rp : jo.rparts) acc = union_sorted(E, acc, rp);
+        jo.rparts.clear();
+        d = acc;
+    } else if (jo.parts.size() == 1 && jo.sorted_unique) {
         newrows.n = jo.parts[0].n;
         newrows.cap = newrows.n;
         newrows.cols = jo.owners[0];
@@ -389,7 +453,7 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
         jo.owners.clear();
         newrows = sort_into_index(E, buf, t, identity_perm(), R.arity);
     }
-    Index d = compute_delta(E, newrows, R.full[0], identity_perm(), R.arity, known_unique);
+    if (!d.cols && d.n == 0) d = compute_delta(E, newrows, R.full[0], identity_perm(), R.arity, known_unique);
     jo.parts.clear();
     jo.owners.clear();
     E.delta_rows += d.n;
@@ -430,14 +494,20 @@ void run_variant(Engine& E, const Variant& v, std::map<uint32_t, PendingOut>& ou
     Relation& H = E.rels[r.head.rel];
     PendingOut& po = outs[r.head.rel];
     JoinOutput jo;
+    if (H.sink != DL_SINK_COUNT)
+        jo.chunk_sink = [&E, &H, &jo](DevPtr buf, TableView t) {
+            Index rp = reduce_part(E, H, buf, t);
+            if (rp.n) jo.rparts.push_back(rp);
+        };
     run_join(E, r, src, H, jo);
-    if (!jo.parts.empty()) {
+    if (!jo.parts.empty() || !jo.rparts.empty()) {
         po.producers++;
-        po.out.sorted_unique = (po.producers == 1) && jo.sorted_unique;
+        po.out.sorted_unique = (po.producers == 1) && jo.sorted_unique && jo.rparts.empty();
         for (size_t i = 0; i < jo.parts.size(); i++) {
             po.out.parts.push_back(jo.parts[i]);
             po.out.owners.push_back(jo.owners[i]);
         }
+        for (Index& rp : jo.rparts) po.out.rparts.push_back(rp);
         if (jo.parts.size() > 1) po.out.sorted_unique = false;
     }
 }
@@ -473,6 +543,7 @@ void fixpoint(Engine& E, dl_stats* st) {
     uint64_t klaunch0[DL_KERNEL_KINDS];
     memcpy(klaunch0, E.klaunch, sizeof(klaunch0));
     validate_program(E);
+    for (Relation& R : E.rels) flush_pending(E, R);
     // plan: index permutations each atom reads; roots for every index a join probes
     for (const Rule& r : E.rules)
         for (uint32_t a = 0; a < r.body.size(); a++) {
@@ -492,6 +563,7 @@ void fixpoint(Engine& E, dl_stats* st) {
     for (auto& R : E.rels) R.stratum = -1;
     for (size_t s = 0; s < E.strata.size(); s++)
         for (uint32_t r : E.strata[s].rels) E.rels[r].stratum = (int)s;
+    E.inst_rounds.assign(E.strata.size(), std::vector<uint32_t>());
 
     for (size_t s = 0; s < E.strata.size(); s++) {
         Stratum& S = E.strata[s];
@@ -507,6 +579,12 @@ void fixpoint(Engine& E, dl_stats* st) {
                     if (E.rels[r.body[j].rel].stratum == (int)s) rec.push_back({&r, (int)j});
             }
         }
+        // Batched form: last[i] = last round in which instance i had a non-empty delta.
+        DArray<uint32_t> last;
+        if (E.instances) {
+            last = E.array<uint32_t>(E.instances);
+            DL_CUDA(cudaMemsetAsync(last.p, 0, sizeof(uint32_t) * E.instances, E.stream));
+        }
         // Round 1: non-recursive rules over full relations; Δ1 = everything now in the stratum.
         std::map<uint32_t, PendingOut> outs;
         for (const Variant& v : round1) run_variant(E, v, outs);
@@ -518,6 +596,7 @@ void fixpoint(Engine& E, dl_stats* st) {
             if (!rec.empty()) {
                 for (size_t k = 0; k < R.perms.size(); k++) R.delta[k] = R.full[k];
                 any = any || R.full[0].n > 0;
+                if (E.instances) mark_runs(E, R.full[0].col(0), R.full[0].n, last.p, 1);
             }
         }
         uint32_t t = 1;
@@ -531,11 +610,22 @@ void fixpoint(Engine& E, dl_stats* st) {
                     Relation& R = E.rels[r];
                     if (R.sink == DL_SINK_COUNT) continue;
                     nd += absorb_round(E, R, outs[r], true);
+                    if (E.instances) mark_runs(E, R.delta[0].col(0), R.delta[0].n, last.p, t);
                 }
                 if (nd == 0) break;
             }
         }
         S.rounds = t;
+        if (E.instances) {
+            std::vector<uint32_t>& ir = E.inst_rounds[s];
+            ir.assign(E.instances, 1);
+            if (!rec.empty()) {
+                DL_CUDA(cudaMemcpyAsync(ir.data(), last.p, sizeof(uint32_t) * E.instances, cudaMemcpyDeviceToHost,
+                                        E.stream));
+                E.sync();
+                for (uint32_t& x : ir) x = x + 1;   // first empty round follows the last non-empty one
+            }
+        }
         for (uint32_t r : S.rels) {
             Relation& R = E.rels[r];
             for (size_t k = 0; k < R.delta.size(); k++) R.delta[k] = empty_index(R.arity, R.perms[k]);
@@ -601,7 +691,11 @@ Relation& rel_of(Engine& E, dl_rel_id r) {
 void load_table(Engine& E, Relation& R, DevPtr buf, TableView t) {
     if (R.sink == DL_SINK_COUNT) throw Error(DL_ERR_STATE, "cannot load facts into a count sink");
     update_max_value(E, t);
-    add_rows(E, R, buf, t);
+    R.pending.push_back({buf, t});
+}
+
+void plain_only(Engine& E, const char* what) {
+    if (E.instances) throw Error(DL_ERR_STATE, std::string(what) + " is not available on a batched engine");
 }
 
 }  // namespace
@@ -641,6 +735,8 @@ int dl_engine_create(const dl_config* cfg, dl_engine** out) {
         E->uuser = c.alloc_user;
         E->flags = c.flags;
         E->tile_units = c.tile_units ? c.tile_units : 4096;
+        E->instances = c.instances;
+        if (c.chunk_rows) E->chunk_rows = c.chunk_rows;
         DL_CUDA(cudaMallocHost(&E->host_scratch, 64 * sizeof(uint64_t)));
         if (!E->ualloc) {
             cudaMemPoolProps props;
@@ -678,15 +774,17 @@ const char* dl_last_error(const dl_engine* e) {
 int dl_relation_create(dl_engine* e, const char* name, uint32_t arity, dl_rel_id* out) {
     return guard(e, [&](Engine& E) {
         if (!name || !*name) throw Error(DL_ERR_ARG, "empty relation name");
-        if (arity < 1 || arity > DL_MAX_ARITY) throw Error(DL_ERR_ARG, "arity out of range");
+        const uint32_t stored = arity + (E.instances ? 1 : 0);
+        if (arity < 1 || stored > DL_MAX_ARITY) throw Error(DL_ERR_ARG, "arity out of range");
         for (auto& r : E.rels)
             if (r.name == name) throw Error(DL_ERR_ARG, std::string("duplicate relation name ") + name);
         Relation R;
         R.name = name;
-        R.arity = arity;
+        R.arity = stored;
+        R.user_arity = arity;
         R.perms.push_back(identity_perm());
-        R.full.push_back(empty_index(arity, identity_perm()));
-        R.delta.push_back(empty_index(arity, identity_perm()));
+        R.full.push_back(empty_index(stored, identity_perm()));
+        R.delta.push_back(empty_index(stored, identity_perm()));
         R.root_needed.push_back(false);
         E.rels.push_back(std::move(R));
         if (out) *out = (dl_rel_id)(E.rels.size() - 1);
@@ -697,13 +795,16 @@ int dl_relation_set_sink(dl_engine* e, dl_rel_id rel, uint32_t sink) {
     return guard(e, [&](Engine& E) {
         Relation& R = rel_of(E, rel);
         if (sink != DL_SINK_STORE && sink != DL_SINK_COUNT) throw Error(DL_ERR_ARG, "bad sink");
-        if (sink == DL_SINK_COUNT && R.full[0].n) throw Error(DL_ERR_STATE, "relation already holds tuples");
+        if (sink == DL_SINK_COUNT && (R.full[0].n || !R.pending.empty()))
+            throw Error(DL_ERR_STATE, "relation already holds tuples");
+        if (sink == DL_SINK_COUNT && E.instances) throw Error(DL_ERR_STATE, "count sinks are not available on a batched engine");
         R.sink = sink;
     });
 }
 
 int dl_load_facts(dl_engine* e, dl_rel_id rel, const uint32_t* const* cols, uint64_t nrows) {
     return guard(e, [&](Engine& E) {
+        plain_only(E, "dl_load_facts");
         Relation& R = rel_of(E, rel);
         if (nrows == 0) return;
         if (!cols) throw Error(DL_ERR_ARG, "null column array");
@@ -735,7 +836,7 @@ int dl_load_facts_rows(dl_engine* e, dl_rel_id rel, const uint32_t* rows, uint64
         E.err = "null rows";
         return DL_ERR_ARG;
     }
-    const uint32_t a = E.rels[rel].arity;
+    const uint32_t a = E.rels[rel].user_arity;
     std::vector<std::vector<uint32_t>> cols(a, std::vector<uint32_t>(nrows));
     for (uint64_t i = 0; i < nrows; i++)
         for (uint32_t c = 0; c < a; c++) cols[c][i] = rows[i * a + c];
@@ -746,6 +847,7 @@ int dl_load_facts_rows(dl_engine* e, dl_rel_id rel, const uint32_t* rows, uint64
 
 int dl_load_facts_device(dl_engine* e, dl_rel_id rel, const uint32_t* const* dcols, uint64_t nrows) {
     return guard(e, [&](Engine& E) {
+        plain_only(E, "dl_load_facts_device");
         Relation& R = rel_of(E, rel);
         if (nrows == 0) return;
         if (!dcols) throw Error(DL_ERR_ARG, "null column array");
@@ -767,6 +869,7 @@ int dl_load_facts_device(dl_engine* e, dl_rel_id rel, const uint32_t* const* dco
 int dl_relation_clear(dl_engine* e, dl_rel_id rel) {
     return guard(e, [&](Engine& E) {
         Relation& R = rel_of(E, rel);
+        R.pending.clear();
         for (size_t k = 0; k < R.perms.size(); k++) {
             R.full[k] = empty_index(R.arity, R.perms[k]);
             R.delta[k] = empty_index(R.arity, R.perms[k]);
@@ -785,7 +888,7 @@ int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t
         Rule r;
         auto read = [&](const dl_atom& a, RuleAtom& ra) {
             Relation& R = rel_of(E, a.rel);
-            if (a.arity != R.arity) throw Error(DL_ERR_ARG, "arity mismatch for relation " + R.name);
+            if (a.arity != R.user_arity) throw Error(DL_ERR_ARG, "arity mismatch for relation " + R.name);
             if (!a.terms) throw Error(DL_ERR_ARG, "null terms");
             ra.rel = a.rel;
             ra.arity = a.arity;
@@ -816,7 +919,7 @@ int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t
         for (uint32_t c = 0; c < r.head.arity; c++)
             if (r.head.terms[c].kind == DL_TERM_VAR && !bvars.count(r.head.terms[c].id))
                 throw Error(DL_ERR_ARG, "head variable not bound by the body");
-        if (bvars.size() > DL_MAX_VARS) throw Error(DL_ERR_ARG, "too many variables");
+        if (bvars.size() + (E.instances ? 1 : 0) > DL_MAX_VARS) throw Error(DL_ERR_ARG, "too many variables");
         if (!var_order || nvars != bvars.size()) throw Error(DL_ERR_ARG, "variable order must list every body variable once");
         std::set<uint32_t> ord(var_order, var_order + nvars);
         if (ord != bvars) throw Error(DL_ERR_ARG, "variable order is not a permutation of the body variables");
@@ -824,6 +927,19 @@ int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t
         if (unsupported_repeat)
             throw Error(DL_ERR_UNSUPPORTED, "a variable repeated within one body atom is not supported on the GPU path");
         r.order.assign(var_order, var_order + nvars);
+        if (E.instances) {
+            // batched form: the instance id is column 0 of every atom and the first join variable
+            const uint32_t inst_var = 0x7fffffffu;
+            auto shift = [&](RuleAtom& ra) {
+                for (uint32_t c = ra.arity; c > 0; c--) ra.terms[c] = ra.terms[c - 1];
+                ra.terms[0].kind = DL_TERM_VAR;
+                ra.terms[0].id = inst_var;
+                ra.arity++;
+            };
+            for (RuleAtom& b : r.body) shift(b);
+            shift(r.head);
+            r.order.insert(r.order.begin(), inst_var);
+        }
         for (uint32_t c = 0; c < r.head.arity; c++)
             if (r.head.terms[c].kind == DL_TERM_CONST) {
                 if (r.head.terms[c].id == 0xffffffffu) throw Error(DL_ERR_UNSUPPORTED, "value 0xFFFFFFFF is reserved");
@@ -862,14 +978,17 @@ int dl_relation_size(dl_engine* e, dl_rel_id rel, uint64_t* nrows) {
     return guard(e, [&](Engine& E) {
         Relation& R = rel_of(E, rel);
         if (!nrows) throw Error(DL_ERR_ARG, "null output");
+        flush_pending(E, R);
         *nrows = R.sink == DL_SINK_COUNT ? R.sink_count : R.full[0].n;
     });
 }
 
 static int fetch_impl(dl_engine* e, dl_rel_id rel, uint32_t* const* cols, uint64_t cap, uint64_t* nrows, bool device) {
     return guard(e, [&](Engine& E) {
+        plain_only(E, "dl_fetch");
         Relation& R = rel_of(E, rel);
         if (R.sink == DL_SINK_COUNT) throw Error(DL_ERR_STATE, "count sinks hold no tuples; use dl_fetch_digest");
+        flush_pending(E, R);
         const Index& ix = R.full[0];
         if (nrows) *nrows = ix.n;
         if (!cols) return;
@@ -896,6 +1015,7 @@ int dl_fetch_digest(dl_engine* e, dl_rel_id rel, uint64_t* count, uint64_t diges
     return guard(e, [&](Engine& E) {
         Relation& R = rel_of(E, rel);
         if (!count || !digest) throw Error(DL_ERR_ARG, "null output");
+        flush_pending(E, R);
         if (R.sink == DL_SINK_COUNT) {
             *count = R.sink_count;
             digest[0] = R.sink_digest[0];
@@ -909,6 +1029,63 @@ int dl_fetch_digest(dl_engine* e, dl_rel_id rel, uint64_t* count, uint64_t diges
         *count = h[0];
         digest[0] = h[1];
         digest[1] = h[2];
+    });
+}
+
+int dl_load_facts_instance(dl_engine* e, dl_rel_id rel, uint32_t inst, const uint32_t* const* cols, uint64_t nrows) {
+    return guard(e, [&](Engine& E) {
+        if (!E.instances) throw Error(DL_ERR_STATE, "dl_load_facts_instance needs a batched engine");
+        Relation& R = rel_of(E, rel);
+        if (inst >= E.instances) throw Error(DL_ERR_ARG, "instance out of range");
+        if (nrows == 0) return;
+        if (!cols) throw Error(DL_ERR_ARG, "null column array");
+        for (uint32_t c = 0; c < R.user_arity; c++)
+            if (!cols[c]) throw Error(DL_ERR_ARG, "null column pointer");
+        if (nrows >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "2^32 rows or more in one load");
+        DevPtr buf = E.make(sizeof(uint32_t) * R.arity * nrows);
+        TableView t;
+        memset(&t, 0, sizeof(t));
+        t.arity = R.arity;
+        t.n = nrows;
+        for (uint32_t c = 0; c < R.arity; c++) t.col[c] = (uint32_t*)buf->ptr + (size_t)c * nrows;
+        fill_u32(E, t.col[0], nrows, inst);
+        for (uint32_t c = 0; c < R.user_arity; c++)
+            DL_CUDA(cudaMemcpyAsync(t.col[c + 1], cols[c], sizeof(uint32_t) * nrows, cudaMemcpyHostToDevice, E.stream));
+        load_table(E, R, buf, t);
+    });
+}
+
+int dl_fetch_instance(dl_engine* e, dl_rel_id rel, uint32_t inst, uint32_t* const* cols_out, uint64_t cap_rows,
+                      uint64_t* nrows_out) {
+    return guard(e, [&](Engine& E) {
+        if (!E.instances) throw Error(DL_ERR_STATE, "dl_fetch_instance needs a batched engine");
+        Relation& R = rel_of(E, rel);
+        if (inst >= E.instances) throw Error(DL_ERR_ARG, "instance out of range");
+        flush_pending(E, R);
+        const Index& ix = R.full[0];
+        uint64_t lo = 0, hi = 0;
+        find_range(E, ix.col(0), ix.n, inst, &lo, &hi);
+        if (nrows_out) *nrows_out = hi - lo;
+        if (!cols_out) return;
+        if (cap_rows < hi - lo) throw Error(DL_ERR_ARG, "cap_rows smaller than the instance's relation");
+        for (uint32_t c = 0; c < R.user_arity; c++) {
+            if (!cols_out[c]) throw Error(DL_ERR_ARG, "null column pointer");
+            if (hi > lo)
+                DL_CUDA(cudaMemcpyAsync(cols_out[c], ix.col((int)c + 1) + lo, sizeof(uint32_t) * (hi - lo),
+                                        cudaMemcpyDeviceToHost, E.stream));
+        }
+        E.sync();
+    });
+}
+
+int dl_instance_rounds(dl_engine* e, uint32_t inst, uint32_t* rounds, uint32_t cap, uint32_t* nstrata) {
+    return guard(e, [&](Engine& E) {
+        if (!E.instances) throw Error(DL_ERR_STATE, "dl_instance_rounds needs a batched engine");
+        if (inst >= E.instances) throw Error(DL_ERR_ARG, "instance out of range");
+        if (nstrata) *nstrata = (uint32_t)E.inst_rounds.size();
+        if (rounds)
+            for (uint32_t s = 0; s < E.inst_rounds.size() && s < cap; s++)
+                rounds[s] = E.inst_rounds[s].empty() ? 0 : E.inst_rounds[s][inst];
     });
 }
 

@@ -179,6 +179,15 @@ void table_digest(Engine& E, const TableView& t, unsigned long long* d);
 // Gather columns: out.col[k] = in.col[perm[k]] (a device copy).
 void permute_copy(Engine& E, const TableView& in, const uint8_t* perm, const TableView& out);
 
+// out[i] = v for i < n.
+void fill_u32(Engine& E, uint32_t* out, uint64_t n, uint32_t v);
+
+// For a table sorted on col0: last[col0[i]] = t for the first row of every run.
+void mark_runs(Engine& E, const uint32_t* col0, uint64_t n, uint32_t* last, uint32_t t);
+
+// [lower_bound, upper_bound) of v in the sorted column col0[0..n) (synchronises).
+void find_range(Engine& E, const uint32_t* col0, uint64_t n, uint32_t v, uint64_t* lo, uint64_t* hi);
+
 // Check that rows are strictly increasing; returns number of violations (synchronises).
 uint64_t count_order_violations(Engine& E, const TableView& t);
 

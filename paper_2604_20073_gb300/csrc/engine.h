@@ -2,6 +2,7 @@
 #pragma once
 
 #include <array>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -19,7 +20,9 @@ inline Perm identity_perm() {
 
 struct Relation {
     std::string name;
-    uint32_t arity = 0;
+    uint32_t arity = 0;               // stored columns (batched form: user columns + instance)
+    uint32_t user_arity = 0;
+    std::vector<std::pair<DevPtr, TableView>> pending;   // loaded rows not yet merged
     uint32_t sink = DL_SINK_STORE;
     std::vector<Perm> perms;          // perms[0] is the identity (canonical order)
     std::vector<Index> full;          // one index per perm; full[0] is always valid
@@ -74,6 +77,9 @@ class Engine {
     std::vector<Rule> rules;
     std::vector<Stratum> strata;
     uint32_t V = 0;                   // values seen so far are < V
+    uint32_t instances = 0;           // batched form: number of instances (0 = one program)
+    uint64_t chunk_rows = 1ull << 30; // larger rule outputs are written and reduced in chunks
+    std::vector<std::vector<uint32_t>> inst_rounds;   // batched form: [stratum][instance]
     uint64_t* host_scratch = nullptr; // pinned, 64 words
     uint64_t launches = 0;
     uint64_t join_rows = 0, count_rows = 0, delta_rows = 0;
@@ -142,7 +148,11 @@ struct RulePlan;
 struct JoinOutput {
     std::vector<TableView> parts;     // each part: arity columns
     std::vector<DevPtr> owners;
-    bool sorted_unique = true;        // rows of each part are sorted (canonical) and distinct
+    std::vector<Index> rparts;        // parts already sorted, deduplicated and anti-joined with full
+    bool sorted_unique = true;        // a single unreduced part is sorted (canonical) and distinct
+    // Receives an output chunk of a rule whose output exceeds the chunk size; it reduces the
+    // chunk and appends it as a reduced part.
+    std::function<void(DevPtr, TableView)> chunk_sink;
 };
 void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Relation& head, JoinOutput& out);
 

@@ -333,6 +333,31 @@ __global__ void k_order_violations(TableView t, unsigned long long* out) {
     if (c) atomicAdd(out, c);
 }
 
+__global__ void k_fill_u32(uint32_t* __restrict__ out, uint64_t n, uint32_t v) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = v;
+}
+
+__global__ void k_mark_runs(const uint32_t* __restrict__ col0, uint64_t n, uint32_t* __restrict__ last, uint32_t t) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        if (i == 0 || col0[i] != col0[i - 1]) last[col0[i]] = t;
+}
+
+__global__ void k_find_range(const uint32_t* __restrict__ col0, uint64_t n, uint32_t v, unsigned long long* out) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (col0[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    uint64_t lo2 = lo, hi2 = n;
+    while (lo2 < hi2) {
+        uint64_t mid = (lo2 + hi2) >> 1;
+        if (col0[mid] <= v) lo2 = mid + 1; else hi2 = mid;
+    }
+    out[0] = lo;
+    out[1] = lo2;
+}
+
 unsigned grid_for(uint64_t n, int threads, unsigned cap = 152u * 16u) {
     uint64_t g = (n + threads - 1) / threads;
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, cap));
@@ -450,6 +475,36 @@ void permute_copy(Engine& E, const TableView& in, const uint8_t* perm, const Tab
         if (in.n)
             DL_CUDA(cudaMemcpyAsync(out.col[k], in.col[perm[k]], sizeof(uint32_t) * in.n, cudaMemcpyDeviceToDevice,
                                     E.stream));
+}
+
+void fill_u32(Engine& E, uint32_t* out, uint64_t n, uint32_t v) {
+    if (!n) return;
+    KernelScope ks(E, DL_K_OTHER, 4 * n);
+    k_fill_u32<<<grid_for(n, 256), 256, 0, E.stream>>>(out, n, v);
+    DL_CHECK_LAUNCH();
+}
+
+void mark_runs(Engine& E, const uint32_t* col0, uint64_t n, uint32_t* last, uint32_t t) {
+    if (!n) return;
+    KernelScope ks(E, DL_K_OTHER, 8 * n);
+    k_mark_runs<<<grid_for(n, 256), 256, 0, E.stream>>>(col0, n, last, t);
+    DL_CHECK_LAUNCH();
+}
+
+void find_range(Engine& E, const uint32_t* col0, uint64_t n, uint32_t v, uint64_t* lo, uint64_t* hi) {
+    if (!n) {
+        *lo = *hi = 0;
+        return;
+    }
+    auto r = E.array<uint64_t>(2);
+    {
+        KernelScope ks(E, DL_K_OTHER, 256);
+        k_find_range<<<1, 1, 0, E.stream>>>(col0, n, v, (unsigned long long*)r.p);
+        DL_CHECK_LAUNCH();
+    }
+    const uint64_t* h = E.readback(r.p, 2);
+    *lo = h[0];
+    *hi = h[1];
 }
 
 uint64_t count_order_violations(Engine& E, const TableView& t) {

@@ -61,6 +61,8 @@ struct LevelParams {
     uint8_t* drv;                         // per entry: driving source
     uint64_t T;
     uint64_t tile;
+    uint64_t tile_base;                   // first tile of this launch (chunked writes)
+    uint64_t out_base;                    // output offset of tile_base (chunked writes)
     uint32_t naive;                       // one frontier entry per CTA (ablation baseline)
     unsigned long long* block_count;      // count pass: per-tile counts; write pass: exclusive offsets
     int mode;
@@ -199,7 +201,7 @@ __device__ __forceinline__ void tile_bounds(const LevelParams& P, uint64_t& lo, 
         lo = e ? P.C[e - 1] : 0;
         hi = P.C[e];
     } else {
-        lo = (uint64_t)blockIdx.x * P.tile;
+        lo = (P.tile_base + blockIdx.x) * P.tile;
         hi = min(lo + P.tile, P.T);
     }
 }
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_write(const __grid_con
     uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
     tile_entries(P, tlo, thi, e0, e1);
-    uint64_t run = P.block_count[blockIdx.x];
+    uint64_t run = P.block_count[P.tile_base + blockIdx.x] - P.out_base;
     Unit U;
     for (uint64_t base = tlo; base < thi; base += blockDim.x) {
         const uint64_t u = base + threadIdx.x;
@@ -630,24 +632,58 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
 
         // Phase 3: allocate exactly and write
         if (last) {
-            if (total >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "rule output of 2^32 rows or more in one round");
-            auto buf = E.make(sizeof(uint32_t) * R.head.arity * total);
-            TableView tv;
-            memset(&tv, 0, sizeof(tv));
-            tv.arity = R.head.arity;
-            tv.n = total;
-            for (uint32_t c = 0; c < R.head.arity; c++) {
-                tv.col[c] = (uint32_t*)buf->ptr + (size_t)c * total;
-                P.ocol[c] = tv.col[c];
-            }
-            {
-                KernelScope ks(E, DL_K_JOIN_WRITE, 4 * T + (entry_bytes + 9) * nF + 4ull * R.head.arity * total);
-                k_wcoj_write<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
-                DL_CHECK_LAUNCH();
-            }
-            out.parts.push_back(tv);
-            out.owners.push_back(buf);
             E.join_rows += total;
+            // Outputs above chunk_rows are written one tile range at a time; each chunk goes to
+            // the caller's chunk sink (sorted, deduplicated, anti-joined) before the next.
+            std::vector<uint64_t> off;
+            const bool chunked = total > E.chunk_rows && out.chunk_sink;
+            if (total >= (1ull << 32) && !chunked)
+                throw Error(DL_ERR_CAPACITY, "rule output of 2^32 rows or more in one round");
+            if (chunked) {
+                off.resize(ntiles + 1);
+                DL_CUDA(cudaMemcpyAsync(off.data(), bc.p, sizeof(uint64_t) * (ntiles + 1), cudaMemcpyDeviceToHost,
+                                        E.stream));
+                E.sync();
+            } else {
+                off = {0, total};
+            }
+            const uint64_t nt = chunked ? ntiles : 1;
+            uint64_t a = 0;
+            while (a < nt) {
+                uint64_t b = chunked ? (uint64_t)(std::upper_bound(off.begin() + a + 1, off.end(), off[a] + E.chunk_rows) -
+                                                  off.begin()) - 1
+                                     : 1;
+                if (b <= a) b = a + 1;
+                const uint64_t rows = off[b] - off[a];
+                if (rows) {
+                    auto buf = E.make(sizeof(uint32_t) * R.head.arity * rows);
+                    TableView tv;
+                    memset(&tv, 0, sizeof(tv));
+                    tv.arity = R.head.arity;
+                    tv.n = rows;
+                    for (uint32_t c = 0; c < R.head.arity; c++) {
+                        tv.col[c] = (uint32_t*)buf->ptr + (size_t)c * rows;
+                        P.ocol[c] = tv.col[c];
+                    }
+                    P.tile_base = chunked ? a : 0;
+                    P.out_base = off[a];
+                    const uint64_t grid = chunked ? b - a : ntiles;
+                    {
+                        KernelScope ks(E, DL_K_JOIN_WRITE,
+                                       (4 * T + (entry_bytes + 9) * nF) * grid / ntiles + 4ull * R.head.arity * rows);
+                        k_wcoj_write<<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
+                        DL_CHECK_LAUNCH();
+                    }
+                    if (chunked) {
+                        out.chunk_sink(buf, tv);
+                    } else {
+                        out.parts.push_back(tv);
+                        out.owners.push_back(buf);
+                    }
+                }
+                a = b;
+            }
+            P.tile_base = P.out_base = 0;
             E.phase_end(0);
             return;
         }

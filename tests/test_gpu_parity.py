@@ -94,6 +94,16 @@ def test_points_to_synthetic(f):
     check(P.POINTS_TO_RELS, facts, P.POINTS_TO)
 
 
+@pytest.mark.parametrize("chunk_rows", [1, 997, 50000])
+def test_chunked_rule_output(chunk_rows):
+    # rule outputs larger than chunk_rows are written, deduplicated and anti-joined in chunks
+    facts = dg.points_to_facts(1 / 4096, 1002)
+    facts = {k: v for k, v in facts.items() if k != "domains"}
+    check(P.POINTS_TO_RELS, facts, P.POINTS_TO, chunk_rows=chunk_rows)
+    e = dg.rmat_edges(2048, 16000, 6)
+    check(P.TC_TRI_RELS, {"E": e}, P.TC_TRI, chunk_rows=chunk_rows)
+
+
 # ------------------------------------------------------- metamorphic checks
 
 @pytest.mark.parametrize("order", [["x", "y", "z"], ["y", "x", "z"], ["z", "y", "x"], ["y", "z", "x"]])
