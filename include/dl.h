@@ -284,6 +284,90 @@ int dl_partition_slices(const uint64_t* C, uint64_t K, uint32_t p, uint64_t* fir
 int dl_decode_unit(const uint64_t* C, const uint64_t* d2, uint64_t K, uint64_t g, uint64_t* key,
                    uint64_t* i1, uint64_t* i2);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A request loop over one GPU: requests (a program plus its facts) are submitted from any
+ * thread, admitted in arrival order as soon as a worker slot is free and their device-
+ * memory share fits in the server's budget, evaluated on the slot's own CUDA stream (so the
+ * work of concurrent requests overlaps on the device, in the spirit of the stream-parallel
+ * rule schedule of Section 6), and keep their relations resident on the device until the
+ * client releases them.  A request that outgrows its share fails alone with
+ * DL_ERR_CAPACITY; others are not disturbed.  The paper evaluates one program at a time;
+ * this loop is an addition for serving many programs. */
+typedef struct dl_server dl_server;
+
+typedef struct dl_server_config {
+    int device;               /* CUDA device ordinal; -1 = current */
+    uint64_t budget_bytes;    /* device memory all admitted requests may hold together; 0 = 90% free */
+    uint32_t max_slots;       /* concurrent requests (worker threads / streams); 0 = 8 */
+    uint32_t flags;           /* DL_FLAG_* for every request's engine */
+    uint64_t default_share;   /* share of a request that states none; 0 = 1 GiB */
+} dl_server_config;
+
+typedef struct dl_rule_spec {
+    dl_atom head;
+    const dl_atom* body;
+    uint32_t nbody;
+    const uint32_t* var_order;
+    uint32_t nvars;
+} dl_rule_spec;
+
+typedef struct dl_fact_spec {
+    dl_rel_id rel;            /* index into the request's relation list */
+    const uint32_t* rows;     /* HOST, row-major, nrows * arity values */
+    uint64_t nrows;
+} dl_fact_spec;
+
+typedef struct dl_request {
+    uint32_t nrel;
+    const char* const* rel_names;   /* relation i has id i inside the request */
+    const uint32_t* rel_arity;
+    const uint32_t* rel_sink;       /* DL_SINK_* per relation, or NULL (all stored) */
+    uint32_t nrules;
+    const dl_rule_spec* rules;
+    uint32_t nfacts;
+    const dl_fact_spec* facts;
+    uint64_t share_bytes;           /* device memory the request may use; 0 = server default */
+} dl_request;
+
+#define DL_REQ_QUEUED 0
+#define DL_REQ_RUNNING 1
+#define DL_REQ_DONE 2
+
+typedef struct dl_server_stats {
+    uint64_t submitted, admitted, completed, failed;
+    uint64_t reserved_bytes, peak_reserved_bytes;
+    uint32_t running, queued;
+} dl_server_stats;
+
+/* Create / destroy a server (destroy waits for running requests and frees everything). */
+int dl_server_create(const dl_server_config* cfg, dl_server** out);
+void dl_server_destroy(dl_server* s);
+
+/* Submit a request (thread-safe).  Everything the request points to is copied before the
+ * call returns.  *ticket identifies it.  Errors: DL_ERR_ARG (malformed request, share above
+ * the whole budget). */
+int dl_server_submit(dl_server* s, const dl_request* req, uint64_t* ticket);
+
+/* State of a request: *state = DL_REQ_QUEUED / RUNNING / DONE; once DONE, *status is the
+ * dl_* status of its evaluation (thread-safe). */
+int dl_server_poll(dl_server* s, uint64_t ticket, int* state, int* status);
+
+/* Block until the request is DONE; *status as in dl_server_poll (thread-safe). */
+int dl_server_wait(dl_server* s, uint64_t ticket, int* status);
+
+/* Borrow the finished request's engine (relation ids as in the request) for dl_fetch,
+ * dl_fetch_digest, dl_relation_size and dl_stratum_info; valid until dl_server_release.
+ * Errors: DL_ERR_STATE (not DONE). */
+int dl_server_result(dl_server* s, uint64_t ticket, dl_engine** engine);
+
+/* Free a request's device memory and its ticket (after DONE).  A finished request keeps its
+ * share of the budget until it is released, so a client that waits for requests in
+ * submission order should release finished ones as it goes, or admission can stall. */
+int dl_server_release(dl_server* s, uint64_t ticket);
+
+int dl_server_get_stats(dl_server* s, dl_server_stats* out);
+
 /* ------------------------------------------------- allocation-free sort + dedup */
 
 /* The paper has no counterpart to this call.  It serves callers that must not allocate

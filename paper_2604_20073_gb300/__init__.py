@@ -72,6 +72,35 @@ class dl_stats(ctypes.Structure):
                 ("kernels", dl_kernel_stat * len(KERNEL_KINDS))]
 
 
+class dl_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("default_share", ctypes.c_uint64)]
+
+
+class dl_rule_spec(ctypes.Structure):
+    _fields_ = [("head", dl_atom), ("body", ctypes.POINTER(dl_atom)), ("nbody", ctypes.c_uint32),
+                ("var_order", _u32p), ("nvars", ctypes.c_uint32)]
+
+
+class dl_fact_spec(ctypes.Structure):
+    _fields_ = [("rel", ctypes.c_uint32), ("rows", _u32p), ("nrows", ctypes.c_uint64)]
+
+
+class dl_request(ctypes.Structure):
+    _fields_ = [("nrel", ctypes.c_uint32), ("rel_names", ctypes.POINTER(ctypes.c_char_p)),
+                ("rel_arity", _u32p), ("rel_sink", _u32p), ("nrules", ctypes.c_uint32),
+                ("rules", ctypes.POINTER(dl_rule_spec)), ("nfacts", ctypes.c_uint32),
+                ("facts", ctypes.POINTER(dl_fact_spec)), ("share_bytes", ctypes.c_uint64)]
+
+
+class dl_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("reserved_bytes", ctypes.c_uint64),
+                ("peak_reserved_bytes", ctypes.c_uint64), ("running", ctypes.c_uint32), ("queued", ctypes.c_uint32)]
+
+
+DL_REQ_QUEUED, DL_REQ_RUNNING, DL_REQ_DONE = 0, 1, 2
+
 _lock = threading.Lock()
 _lib = None
 
@@ -104,6 +133,15 @@ _SIGS = {
     "dl_fetch_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_u32p),
                                          ctypes.c_uint64, _u64p]),
     "dl_instance_rounds": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p]),
+    "dl_server_create": (ctypes.c_int, [ctypes.POINTER(dl_server_config), ctypes.POINTER(ctypes.c_void_p)]),
+    "dl_server_destroy": (None, [ctypes.c_void_p]),
+    "dl_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_request), _u64p]),
+    "dl_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "dl_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    "dl_server_result": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]),
+    "dl_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "dl_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_server_stats)]),
     "dl_sort_unique_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32, ctypes.c_uint64,
                                               ctypes.POINTER(ctypes.c_void_p), _u64p, ctypes.c_void_p]),
 }
@@ -342,6 +380,131 @@ class Engine:
         d = (ctypes.c_uint64 * 2)()
         self._check(self.lib.dl_fetch_digest(self.h, self.rel_ids[name], ctypes.byref(c), d))
         return (c.value, d[0], d[1])
+
+
+class _Borrowed(Engine):
+    """A finished request's engine, owned by the server (never destroyed from here)."""
+
+    def __init__(self, lib, h, relations: dict):
+        self.lib = lib
+        self.h = h
+        self.instances = 0
+        self.names = list(relations)
+        self.rel_ids = {n: i for i, n in enumerate(self.names)}
+        self.arity = dict(relations)
+
+    def close(self):
+        self.h = None
+
+
+class Server:
+    """Request loop (dl_server_*): submit programs from any thread; results stay on the GPU
+    until released."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, max_slots: int = 8, flags: int = 0,
+                 default_share: int = 0):
+        import torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the Datalog server runs only on the GPU")
+        cfg = dl_server_config(device, budget_bytes, max_slots, flags, default_share)
+        h = ctypes.c_void_p()
+        rc = self.lib.dl_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != DL_OK:
+            raise DatalogError(rc, "dl_server_create failed")
+        self.h = h
+        self.req_relations: dict = {}
+
+    def submit(self, relations: dict, facts: dict, rules: list, sinks: dict | None = None, share: int = 0) -> int:
+        names = list(relations)
+        rid = {n: i for i, n in enumerate(names)}
+        keep = []
+        cnames = (ctypes.c_char_p * len(names))(*[n.encode() for n in names])
+        arity = (ctypes.c_uint32 * len(names))(*[relations[n] for n in names])
+        sink = (ctypes.c_uint32 * len(names))(*[(sinks or {}).get(n, DL_SINK_STORE) for n in names])
+        rs = (dl_rule_spec * len(rules))()
+        for k, r in enumerate(rules):
+            var_ids: dict = {}
+
+            def atom(a):
+                rel, terms = a
+                ts = (dl_term * len(terms))()
+                for i, t in enumerate(terms):
+                    if isinstance(t, str):
+                        ts[i].kind, ts[i].id = DL_TERM_VAR, var_ids.setdefault(t, len(var_ids))
+                    else:
+                        ts[i].kind, ts[i].id = DL_TERM_CONST, int(t)
+                keep.append(ts)
+                out = dl_atom()
+                out.rel, out.arity, out.terms = rid[rel], len(terms), ts
+                return out
+            body = (dl_atom * len(r[1]))(*[atom(b) for b in r[1]])
+            head = atom(r[0])
+            order = (ctypes.c_uint32 * len(r[2]))(*[var_ids.get(v, 1023) for v in r[2]])
+            keep += [body, order]
+            rs[k].head, rs[k].body, rs[k].nbody = head, body, len(r[1])
+            rs[k].var_order, rs[k].nvars = order, len(r[2])
+        fs = (dl_fact_spec * len(facts))()
+        for k, (name, rows) in enumerate(facts.items()):
+            rows = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32).reshape(-1, relations[name]))
+            keep.append(rows)
+            fs[k].rel, fs[k].rows, fs[k].nrows = rid[name], rows.ctypes.data_as(_u32p), rows.shape[0]
+        req = dl_request(len(names), cnames, arity, sink, len(rules), rs, len(facts), fs, share)
+        t = ctypes.c_uint64()
+        rc = self.lib.dl_server_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if rc != DL_OK:
+            raise DatalogError(rc, "dl_server_submit failed")
+        self.req_relations[t.value] = dict(relations)
+        return t.value
+
+    def poll(self, ticket: int) -> tuple:
+        st, status = ctypes.c_int(), ctypes.c_int()
+        rc = self.lib.dl_server_poll(self.h, ticket, ctypes.byref(st), ctypes.byref(status))
+        if rc != DL_OK:
+            raise DatalogError(rc, "dl_server_poll failed")
+        return st.value, status.value
+
+    def wait(self, ticket: int) -> int:
+        status = ctypes.c_int()
+        rc = self.lib.dl_server_wait(self.h, ticket, ctypes.byref(status))
+        if rc != DL_OK:
+            raise DatalogError(rc, "dl_server_wait failed")
+        return status.value
+
+    def result(self, ticket: int) -> Engine:
+        e = ctypes.c_void_p()
+        rc = self.lib.dl_server_result(self.h, ticket, ctypes.byref(e))
+        if rc != DL_OK:
+            raise DatalogError(rc, "dl_server_result failed")
+        return _Borrowed(self.lib, e, self.req_relations[ticket])
+
+    def release(self, ticket: int):
+        rc = self.lib.dl_server_release(self.h, ticket)
+        if rc != DL_OK:
+            raise DatalogError(rc, "dl_server_release failed")
+        self.req_relations.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = dl_server_stats()
+        self.lib.dl_server_get_stats(self.h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in dl_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dl_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def build_program(eng: Engine, relations: dict, rules: list, sinks: dict | None = None):

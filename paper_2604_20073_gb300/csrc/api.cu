@@ -21,10 +21,6 @@ DevMem::~DevMem() {
     if (ptr) eng->release(ptr, bytes);
 }
 
-namespace {
-std::map<Engine*, cudaMemPool_t> g_pools;  // engine-owned stream-ordered pools
-}
-
 void* Engine::alloc(size_t bytes) {
     if (bytes == 0) bytes = 1;
     bytes = (bytes + 255) & ~size_t(255);
@@ -36,7 +32,7 @@ void* Engine::alloc(size_t bytes) {
         p = ualloc(bytes, stream, uuser);
         if (!p) throw Error(DL_ERR_CAPACITY, "user allocator returned NULL");
     } else {
-        cudaError_t st = cudaMallocFromPoolAsync(&p, bytes, g_pools[this], stream);
+        cudaError_t st = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
         if (st == cudaErrorMemoryAllocation) {
             cudaGetLastError();
             throw Error(DL_ERR_CAPACITY, "device out of memory");
@@ -85,14 +81,11 @@ void Engine::phase_end(int kind) {
 }
 
 Engine::~Engine() {
-    rels.clear();
-    if (stream) cudaStreamSynchronize(stream);
+    rels.clear();                      // stream-ordered frees: no wait needed
     for (auto ev : event_pool) cudaEventDestroy(ev);
-    if (host_scratch) cudaFreeHost(host_scratch);
-    auto it = g_pools.find(this);
-    if (it != g_pools.end()) {
-        cudaMemPoolDestroy(it->second);
-        g_pools.erase(it);
+    if (pool) {
+        cudaStreamSynchronize(stream);  // the pool's memory must be idle before it is destroyed
+        cudaMemPoolDestroy(pool);
     }
     if (own_stream && stream) cudaStreamDestroy(stream);
 }
@@ -737,18 +730,15 @@ int dl_engine_create(const dl_config* cfg, dl_engine** out) {
         E->tile_units = c.tile_units ? c.tile_units : 4096;
         E->instances = c.instances;
         if (c.chunk_rows) E->chunk_rows = c.chunk_rows;
-        DL_CUDA(cudaMallocHost(&E->host_scratch, 64 * sizeof(uint64_t)));
         if (!E->ualloc) {
             cudaMemPoolProps props;
             memset(&props, 0, sizeof(props));
             props.allocType = cudaMemAllocationTypePinned;
             props.location.type = cudaMemLocationTypeDevice;
             props.location.id = E->device;
-            cudaMemPool_t pool;
-            DL_CUDA(cudaMemPoolCreate(&pool, &props));
+            DL_CUDA(cudaMemPoolCreate(&E->pool, &props));
             uint64_t thr = UINT64_MAX;
-            DL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-            g_pools[E] = pool;
+            DL_CUDA(cudaMemPoolSetAttribute(E->pool, cudaMemPoolAttrReleaseThreshold, &thr));
         }
     } catch (const Error& x) {
         int code = x.code;

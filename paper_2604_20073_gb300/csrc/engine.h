@@ -67,6 +67,7 @@ class Engine {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     uint64_t budget = 0, used = 0, peak = 0;
+    cudaMemPool_t pool = nullptr;     // engine-owned stream-ordered pool (no user allocator)
     dl_alloc_fn ualloc = nullptr;
     dl_free_fn ufree = nullptr;
     void* uuser = nullptr;
@@ -80,7 +81,8 @@ class Engine {
     uint32_t instances = 0;           // batched form: number of instances (0 = one program)
     uint64_t chunk_rows = 1ull << 30; // larger rule outputs are written and reduced in chunks
     std::vector<std::vector<uint32_t>> inst_rounds;   // batched form: [stratum][instance]
-    uint64_t* host_scratch = nullptr; // pinned, 64 words
+    uint64_t host_scratch[64] = {0};  // readback target (pageable: freeing pinned memory would
+                                      // synchronise the whole device, stalling other engines)
     uint64_t launches = 0;
     uint64_t join_rows = 0, count_rows = 0, delta_rows = 0;
     bool in_fixpoint = false;
