@@ -239,6 +239,7 @@ def run_batched_workload(args):
     torch.cuda.synchronize()
     clocks = Clocks(0)
     times, launches = [], 0
+    kms = {}
     for _ in range(args.steps):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -248,6 +249,9 @@ def run_batched_workload(args):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
         launches += sum(st["kernel_launches"] for st in sts)
+        for st in sts:
+            for k, v in st["kernels"].items():
+                kms[k] = kms.get(k, 0.0) + v["ms"] / args.steps
     clk = clocks.stop()
     ms = statistics.mean(times)
     sizes_b = {}
@@ -291,7 +295,9 @@ def run_batched_workload(args):
            "results": {"Reach_rows": int(reach_total), "Tri_rows": int(tri_total), "mismatches_vs_alone": mism},
            "per_instance_baseline": {"value": args.instances / (base_ms / 1e3), "unit": "programs/s",
                                      "ms_total": base_ms, "how": "one engine call per instance, same kernels"},
-           "speedup_vs_per_instance": base_ms / ms, "gpu_launches": launches, "clocks": clk}
+           "speedup_vs_per_instance": base_ms / ms, "gpu_launches": launches,
+           "kernels_ms_per_step": {k: round(v, 2) for k, v in kms.items() if v},
+           "rounds_max": max(max(r[1]) for r in sizes_b.values()), "clocks": clk}
     print(json.dumps(out))
 
 

@@ -351,6 +351,231 @@ __global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_write(const __grid_con
     }
 }
 
+// ------------------------------------------------------------ warp-major kernels
+//
+// Used when a level averages at least 32 units per frontier entry.  A warp owns a
+// contiguous range of the unit space and walks the entries overlapping it; the entry's
+// state (driver, source ranges) is loaded once and shared by the 32 lanes, which take the
+// entry's units 32 at a time.  No per-unit decode, and the lanes of a step probe the same
+// ranges.  The count pass leaves one count per warp; after the scan the write pass ranks a
+// step's survivors with a ballot, so output stays in unit order.
+
+constexpr int kWarps = kJoinThreads / 32;
+
+template <int NS>
+struct EntryState {
+    uint64_t e, ebase, eend;
+    const uint32_t* col[NS];
+    const uint32_t* root[NS];
+    uint32_t rootV[NS];
+    uint32_t lo[NS], hi[NS];
+    const uint32_t* dcol;         // the driver's state (scalars; see Walker-free note below)
+    const uint32_t* droot;
+    uint32_t dlo, dhi, dneed;
+    int s0;
+};
+
+__device__ __forceinline__ const uint32_t* dense_root_of(const LevelParams& P, int s, uint32_t& V) {
+    const int a = P.src_atom[s];
+    if (a == kVirtual || P.src_depth[s] != 0 || !P.atom[a].root) {
+        V = 0;
+        return nullptr;
+    }
+    V = P.atom[a].V;
+    return P.atom[a].root;
+}
+
+// The driver is addressed through scalars: selecting it from the per-source arrays by the
+// per-entry index s0 would make the compiler index them dynamically and move them out of
+// registers.
+template <int NS>
+__device__ __forceinline__ void entry_load(const LevelParams& P, EntryState<NS>& S, uint64_t e) {
+    S.e = e;
+    S.ebase = e ? P.C[e - 1] : 0;
+    S.eend = P.C[e];
+    S.s0 = P.drv[e];
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (s < (int)P.nsrc) {
+            uint32_t lo, hi;
+            S.col[s] = src_range(P, s, e, lo, hi);
+            S.root[s] = dense_root_of(P, s, S.rootV[s]);
+            S.lo[s] = lo;
+            S.hi[s] = hi;
+        }
+    }
+    uint32_t dV;
+    S.dcol = src_range(P, S.s0, e, S.dlo, S.dhi);
+    S.droot = dense_root_of(P, S.s0, dV);
+    S.dneed = P.src_need_range[S.s0];
+}
+
+template <int NS>
+__device__ __forceinline__ bool entry_eval(const LevelParams& P, const EntryState<NS>& S, uint64_t u, uint32_t& v,
+                                           uint32_t (&nlo)[NS], uint32_t (&nhi)[NS], uint32_t& dnlo, uint32_t& dnhi) {
+    const uint64_t local = u - S.ebase;
+    bool ok;
+    if (S.droot) {
+        v = (uint32_t)local;                       // iterate the dense value domain
+        dnlo = __ldg(S.droot + v);
+        dnhi = __ldg(S.droot + v + 1);
+        ok = dnlo < dnhi;
+    } else {
+        const uint32_t r = S.dlo + (uint32_t)local;
+        v = __ldg(S.dcol + r);
+        ok = !(r > S.dlo && __ldg(S.dcol + r - 1) == v);   // only the first row of a value
+        dnlo = r;
+        dnhi = (ok && S.dneed) ? upper_bound_u32(S.dcol, r + 1, S.dhi, v) : r + 1;
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (ok && s < (int)P.nsrc && s != S.s0) {
+            if (S.root[s]) {
+                const uint32_t l = v < S.rootV[s] ? __ldg(S.root[s] + v) : 0;
+                const uint32_t h = v < S.rootV[s] ? __ldg(S.root[s] + v + 1) : 0;
+                ok = l < h;
+                nlo[s] = l;
+                nhi[s] = h;
+            } else {
+                const uint32_t l = lower_bound_u32(S.col[s], S.lo[s], S.hi[s], v);
+                ok = l < S.hi[s] && __ldg(S.col[s] + l) == v;
+                nlo[s] = l;
+                nhi[s] = (ok && P.src_need_range[s]) ? upper_bound_u32(S.col[s], l + 1, S.hi[s], v) : l + 1;
+            }
+        }
+    }
+    return ok;
+}
+
+__device__ __forceinline__ void warp_range(const LevelParams& P, uint64_t& wlo, uint64_t& whi) {
+    const uint64_t tlo = (P.tile_base + blockIdx.x) * P.tile;
+    const uint64_t thi = min(tlo + P.tile, P.T);
+    const uint64_t per = (P.tile + kWarps - 1) / kWarps;
+    wlo = min(tlo + (threadIdx.x >> 5) * per, thi);
+    whi = min(wlo + per, thi);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_count_wm(const __grid_constant__ LevelParams P) {
+    const int lane = threadIdx.x & 31;
+    uint64_t wlo, whi;
+    warp_range(P, wlo, whi);
+    unsigned long long cnt = 0, hs = 0, hx = 0;
+    if (wlo < whi) {
+        uint64_t e = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, wlo);
+        EntryState<NS> S;
+        uint64_t u = wlo;
+        for (;;) {
+            entry_load(P, S, e);
+            const uint64_t stop = min(S.eend, whi);
+            for (uint64_t base = u; base < stop; base += 32) {
+                const uint64_t uu = base + lane;
+                uint32_t v, nlo[NS], nhi[NS], dnlo, dnhi;
+                if (uu >= stop || !entry_eval(P, S, uu, v, nlo, nhi, dnlo, dnhi)) continue;
+                cnt++;
+                if (P.mode == MODE_COUNT) {
+                    uint64_t h = kTupleHashSeed;
+                    for (uint32_t c = 0; c < P.head_arity; c++) {
+                        const int pos = P.head_pos[c];
+                        const uint32_t x = pos < 0 ? P.head_const[c] : (pos == (int)P.level ? v : __ldg(P.fval[pos] + e));
+                        h = tuple_hash_step(h, x, c);
+                    }
+                    hs += h;
+                    hx ^= h;
+                }
+            }
+            u = stop;
+            if (u >= whi) break;
+            e++;
+            while (P.C[e] <= u) e++;   // entries without units
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        cnt += __shfl_xor_sync(kFull, cnt, o);
+        hs += __shfl_xor_sync(kFull, hs, o);
+        hx ^= __shfl_xor_sync(kFull, hx, o);
+    }
+    if (lane == 0) {
+        P.block_count[(uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)] = cnt;
+        if (P.mode == MODE_COUNT && cnt) {
+            atomicAdd(&P.digest[0], cnt);
+            atomicAdd(&P.digest[1], hs);
+            atomicXor(&P.digest[2], hx);
+        }
+    }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_write_wm(const __grid_constant__ LevelParams P) {
+    const int lane = threadIdx.x & 31;
+    uint64_t wlo, whi;
+    warp_range(P, wlo, whi);
+    if (wlo >= whi) return;
+    uint64_t o = P.block_count[(P.tile_base + blockIdx.x) * kWarps + (threadIdx.x >> 5)] - P.out_base;
+    uint64_t e = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, wlo);
+    EntryState<NS> S;
+    uint64_t u = wlo;
+    const unsigned lt = (1u << lane) - 1;
+    for (;;) {
+        entry_load(P, S, e);
+        const uint64_t stop = min(S.eend, whi);
+        for (uint64_t base = u; base < stop; base += 32) {
+            const uint64_t uu = base + lane;
+            uint32_t v = 0, nlo[NS], nhi[NS], dnlo = 0, dnhi = 0;
+            const bool f = uu < stop && entry_eval(P, S, uu, v, nlo, nhi, dnlo, dnhi);
+            const unsigned ball = __ballot_sync(kFull, f);
+            if (f) {
+                const uint64_t w = o + __popc(ball & lt);
+                if (P.mode == MODE_HEAD) {
+                    for (uint32_t c = 0; c < P.head_arity; c++) {
+                        const int hp = P.head_pos[c];
+                        P.ocol[c][w] = hp < 0 ? P.head_const[c] : (hp == (int)P.level ? v : __ldg(P.fval[hp] + e));
+                    }
+                } else {
+                    for (uint32_t k = 0; k < P.level; k++) P.oval[k][w] = __ldg(P.fval[k] + e);
+                    P.oval[P.level][w] = v;
+                    if (P.oparent) P.oparent[w] = (uint32_t)e;
+                    for (uint32_t c = 0; c < P.ncarry; c++) {
+                        const int s = P.carry_src[c];
+                        if (s == S.s0) {
+                            P.olo[c][w] = dnlo;
+                            P.ohi[c][w] = dnhi;
+                        } else if (s < 0) {
+                            const int slot = P.carry_slot[c];
+                            P.olo[c][w] = slot >= 0 ? __ldg(P.flo[slot] + e) : 0;
+                            P.ohi[c][w] = slot >= 0 ? __ldg(P.fhi[slot] + e) : P.atom[P.carry_atom[c]].n;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < NS; q++) {
+                        if (q >= (int)P.nsrc || q == S.s0) continue;
+                        for (uint32_t c = 0; c < P.ncarry; c++)
+                            if (P.carry_src[c] == q) {
+                                P.olo[c][w] = nlo[q];
+                                P.ohi[c][w] = nhi[q];
+                            }
+                    }
+                }
+            }
+            o += __popc(ball);
+        }
+        u = stop;
+        if (u >= whi) break;
+        e++;
+        while (P.C[e] <= u) e++;
+    }
+}
+
+#define DL_NS_DISPATCH(KERNEL, NSRC, GRID, STREAM, PARAMS)                                              \
+    do {                                                                                            \
+        if ((NSRC) <= 1) KERNEL<1><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);                  \
+        else if ((NSRC) <= 2) KERNEL<2><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);             \
+        else if ((NSRC) <= 3) KERNEL<3><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);             \
+        else if ((NSRC) <= 4) KERNEL<4><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);             \
+        else KERNEL<kMaxSrc + 1><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);                   \
+    } while (0)
+
 // Sibling runs of a frontier: seg[k] = 1 if entry k starts a new parent's run.
 __global__ void k_seg_flags(const uint32_t* __restrict__ parent, uint64_t n, uint32_t* __restrict__ seg) {
     const uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -597,8 +822,19 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
         P.T = T;
         const uint64_t ntiles = P.naive ? nF : (T + P.tile - 1) / P.tile;
         if (ntiles >= (1ull << 31)) throw Error(DL_ERR_CAPACITY, "join level exceeds 2^31 tiles");
-        auto bc = E.array<uint64_t>(ntiles + 1);
+        // warp-major kernels when entries average >= 32 units (one count per warp)
+        const bool wm = !P.naive && T >= 32 * nF;
+        const uint64_t ncounts = wm ? ntiles * kWarps : ntiles;
+        auto bc = E.array<uint64_t>(ncounts + 1);
         P.block_count = (unsigned long long*)bc.p;
+        auto launch_count = [&]() {
+            if (wm) DL_NS_DISPATCH(k_wcoj_count_wm, P.nsrc, (unsigned)ntiles, E.stream, P);
+            else k_wcoj_count<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+        };
+        auto launch_write = [&](uint64_t grid) {
+            if (wm) DL_NS_DISPATCH(k_wcoj_write_wm, P.nsrc, (unsigned)grid, E.stream, P);
+            else k_wcoj_write<<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
+        };
 
         if (last && count_sink) {
             auto dg = E.array<uint64_t>(3);
@@ -607,7 +843,7 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
             P.digest = (unsigned long long*)dg.p;
             {
                 KernelScope ks(E, DL_K_JOIN_COUNT, 4 * T + (entry_bytes + 9) * nF);
-                k_wcoj_count<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+                launch_count();
                 DL_CHECK_LAUNCH();
             }
             const uint64_t* d = E.readback(dg.p, 3);
@@ -623,11 +859,11 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
         P.mode = last ? MODE_HEAD : MODE_FRONTIER;
         {
             KernelScope ks(E, DL_K_JOIN_COUNT, 4 * T + (entry_bytes + 9) * nF);
-            k_wcoj_count<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+            launch_count();
             DL_CHECK_LAUNCH();
         }
-        scan_u64(E, bc.p, ntiles, false, bc.p + ntiles);
-        const uint64_t total = E.readback(bc.p + ntiles, 1)[0];
+        scan_u64(E, bc.p, ncounts, false, bc.p + ncounts);
+        const uint64_t total = E.readback(bc.p + ncounts, 1)[0];
         if (total == 0) { E.phase_end(0); return; }
 
         // Phase 3: allocate exactly and write
@@ -640,10 +876,12 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
             if (total >= (1ull << 32) && !chunked)
                 throw Error(DL_ERR_CAPACITY, "rule output of 2^32 rows or more in one round");
             if (chunked) {
-                off.resize(ntiles + 1);
-                DL_CUDA(cudaMemcpyAsync(off.data(), bc.p, sizeof(uint64_t) * (ntiles + 1), cudaMemcpyDeviceToHost,
+                std::vector<uint64_t> all(ncounts + 1);
+                DL_CUDA(cudaMemcpyAsync(all.data(), bc.p, sizeof(uint64_t) * (ncounts + 1), cudaMemcpyDeviceToHost,
                                         E.stream));
                 E.sync();
+                off.resize(ntiles + 1);   // output offset of each tile's first unit
+                for (uint64_t t = 0; t <= ntiles; t++) off[t] = all[wm ? t * kWarps : t];
             } else {
                 off = {0, total};
             }
@@ -671,7 +909,7 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
                     {
                         KernelScope ks(E, DL_K_JOIN_WRITE,
                                        (4 * T + (entry_bytes + 9) * nF) * grid / ntiles + 4ull * R.head.arity * rows);
-                        k_wcoj_write<<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
+                        launch_write(grid);
                         DL_CHECK_LAUNCH();
                     }
                     if (chunked) {
@@ -705,7 +943,7 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
         {
             KernelScope ks(E, DL_K_JOIN_WRITE,
                            4 * T + (entry_bytes + 9) * nF + 4ull * (lvl + 1 + 2 * P.ncarry + (next_reuse ? 1 : 0)) * total);
-            k_wcoj_write<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+            launch_write(ntiles);
             DL_CHECK_LAUNCH();
         }
         f_seg = f_segstart = nullptr;

@@ -38,3 +38,11 @@ POINTS_TO = [
      ["w", "h1", "f", "v", "h2"]),
 ]
 POINTS_TO_RELS = {"New": 2, "Assign": 2, "Load": 3, "Store": 3, "VPT": 2, "FPT": 3}
+
+# Same Generation (the paper's Table 3 workload): x and y are siblings, or children of a
+# same-generation pair.
+SG = [
+    (("SG", ["x", "y"]), [("Edge", ["p", "x"]), ("Edge", ["p", "y"])], ["p", "x", "y"]),
+    (("SG", ["x", "y"]), [("Edge", ["a", "x"]), ("SG", ["a", "b"]), ("Edge", ["b", "y"])], ["a", "b", "x", "y"]),
+]
+SG_RELS = {"Edge": 2, "SG": 2}

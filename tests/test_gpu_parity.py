@@ -104,6 +104,19 @@ def test_chunked_rule_output(chunk_rows):
     check(P.TC_TRI_RELS, {"E": e}, P.TC_TRI, chunk_rows=chunk_rows)
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_same_generation(seed):
+    e = dg.rmat_edges(1500, 3000, 700 + seed)
+    got, strata, _ = check(P.SG_RELS, {"Edge": e}, P.SG)
+    assert len(got["SG"]) > len(e)
+
+
+def test_same_generation_tree_closed_form():
+    from tests.test_oracle_pins import kary_tree
+    got, strata, _ = check(P.SG_RELS, {"Edge": kary_tree(3, 5)}, P.SG)
+    assert len(got["SG"]) == sum(3 ** (2 * d) for d in range(1, 6)) and strata == [(["SG"], 6)]
+
+
 # ------------------------------------------------------- metamorphic checks
 
 @pytest.mark.parametrize("order", [["x", "y", "z"], ["y", "x", "z"], ["z", "y", "x"], ["y", "z", "x"]])

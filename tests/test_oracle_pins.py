@@ -94,6 +94,29 @@ def test_points_to_two_heaps_by_hand():
     assert res.rounds_of("VPT") == 5
 
 
+def kary_tree(k, depth):
+    edges, frontier, nxt = [], [0], 1
+    for _ in range(depth):
+        new = []
+        for u in frontier:
+            for _ in range(k):
+                edges.append((u, nxt))
+                new.append(nxt)
+                nxt += 1
+        frontier = new
+    return np.array(edges, dtype=np.uint32).reshape(-1, 2)
+
+
+@pytest.mark.parametrize("k,depth", [(2, 1), (2, 4), (3, 3), (1, 5)])
+def test_same_generation_on_trees(k, depth):
+    # SG holds exactly for pairs at the same depth >= 1.  A pair whose lowest common ancestor
+    # is t >= 1 levels up appears in round t (a node paired with itself: t = 1, through its
+    # parent), so the last productive round is `depth` when k >= 2 and 1 on a path.
+    r = run(P.SG_RELS, {"Edge": kary_tree(k, depth)}, P.SG)
+    assert len(r.relations["SG"]) == sum(k ** (2 * d) for d in range(1, depth + 1))
+    assert r.rounds_of("SG") == (depth if k >= 2 else 1) + 1
+
+
 # ------------------------------------------------------- independent routines
 
 def test_reach_equals_graph_reachability():
