@@ -209,6 +209,8 @@ typedef struct dl_stats {
     double ms_dedup;           /* device time of dedup + anti-join (compute delta) */
     double ms_merge;           /* device time of merges and index rebuilds */
     dl_kernel_stat kernels[DL_KERNEL_KINDS];  /* per kernel kind; zero unless DL_FLAG_PROFILE */
+    uint32_t top_kind;         /* DL_FLAG_PROFILE: kind of the single longest launch */
+    dl_kernel_stat top;        /* that launch (launches = 1) */
 } dl_stats;
 
 /* Evaluate all rules to the least fixpoint (semi-naive, Jacobi rounds: every rule of a

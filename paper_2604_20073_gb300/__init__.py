@@ -69,7 +69,8 @@ class dl_stats(ctypes.Structure):
                 ("peak_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
                 ("ms_total", ctypes.c_double), ("ms_join", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("ms_dedup", ctypes.c_double), ("ms_merge", ctypes.c_double),
-                ("kernels", dl_kernel_stat * len(KERNEL_KINDS))]
+                ("kernels", dl_kernel_stat * len(KERNEL_KINDS)), ("top_kind", ctypes.c_uint32),
+                ("top", dl_kernel_stat)]
 
 
 class dl_server_config(ctypes.Structure):
@@ -326,7 +327,9 @@ class Engine:
     def fixpoint(self) -> dict:
         st = dl_stats()
         self._check(self.lib.dl_fixpoint(self.h, ctypes.byref(st)))
-        out = {f: getattr(st, f) for f, _ in dl_stats._fields_ if f not in ("rounds", "stratum_first_rel", "kernels")}
+        out = {f: getattr(st, f) for f, _ in dl_stats._fields_
+               if f not in ("rounds", "stratum_first_rel", "kernels", "top", "top_kind")}
+        out["top"] = {"kind": KERNEL_KINDS[st.top_kind], "ms": st.top.ms, "alg_bytes": st.top.alg_bytes}
         out["rounds"] = list(st.rounds[: min(st.nstrata, DL_MAX_STRATA)])
         out["kernels"] = {k: {"launches": st.kernels[i].launches, "ms": st.kernels[i].ms,
                               "alg_bytes": st.kernels[i].alg_bytes} for i, k in enumerate(KERNEL_KINDS)}

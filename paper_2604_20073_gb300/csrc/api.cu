@@ -649,8 +649,15 @@ void fixpoint(Engine& E, dl_stats* st) {
         for (int k = 0; k < DL_KERNEL_KINDS; k++) st->kernels[k].launches = E.klaunch[k] - klaunch0[k];
         for (const KernelEvent& ke : E.kev) {
             float f = 0;
-            if (cudaEventElapsedTime(&f, ke.a, ke.b) == cudaSuccess) st->kernels[ke.kind].ms += f;
+            if (cudaEventElapsedTime(&f, ke.a, ke.b) != cudaSuccess) continue;
+            st->kernels[ke.kind].ms += f;
             st->kernels[ke.kind].alg_bytes += ke.bytes;
+            if (f > st->top.ms) {
+                st->top_kind = (uint32_t)ke.kind;
+                st->top.launches = 1;
+                st->top.ms = f;
+                st->top.alg_bytes = ke.bytes;
+            }
         }
         st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
