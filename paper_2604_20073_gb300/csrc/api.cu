@@ -140,26 +140,34 @@ Index empty_index(uint32_t arity, const Perm& perm) {
 }
 
 // Sort a table (canonical column order of its index) in place; returns an Index holding it.
-// `buf` owns t's columns; the result owns whichever buffer ends up holding the sorted rows.
-Index sort_into_index(Engine& E, DevPtr buf, TableView t, const Perm& perm, uint32_t arity) {
+// `buf` owns t's columns, which lie `stride` values apart (0: t.n apart); the result owns
+// whichever buffer ends up holding the sorted rows.
+Index sort_into_index(Engine& E, DevPtr buf, TableView t, const Perm& perm, uint32_t arity, uint64_t stride = 0) {
+    if (!stride) stride = std::max<uint64_t>(t.n, 1);
     Index ix = empty_index(arity, perm);
     ix.n = t.n;
-    ix.cap = std::max<uint64_t>(t.n, 1);
+    ix.cap = stride;
     if (t.n <= 1) {
         ix.cols = buf;
         return ix;
     }
-    DevPtr tmpbuf = E.make(sizeof(uint32_t) * arity * ix.cap);
+    const uint64_t tcap = std::max<uint64_t>(t.n, 1);
+    DevPtr tmpbuf = E.make(sizeof(uint32_t) * arity * tcap);
     TableView tmp;
     memset(&tmp, 0, sizeof(tmp));
     tmp.arity = arity;
     tmp.n = t.n;
-    for (uint32_t c = 0; c < arity; c++) tmp.col[c] = (uint32_t*)tmpbuf->ptr + (size_t)c * ix.cap;
+    for (uint32_t c = 0; c < arity; c++) tmp.col[c] = (uint32_t*)tmpbuf->ptr + (size_t)c * tcap;
     uint32_t* orig0 = t.col[0];
     E.phase_begin(1);
     radix_sort_rows(E, t, tmp, nullptr);
     E.phase_end(1);
-    ix.cols = (t.col[0] == orig0) ? buf : tmpbuf;
+    if (t.col[0] != orig0) {
+        ix.cols = tmpbuf;
+        ix.cap = tcap;
+    } else {
+        ix.cols = buf;
+    }
     return ix;
 }
 
@@ -379,6 +387,25 @@ struct PendingOut {
     uint32_t producers = 0;   // variants that produced parts
 };
 
+// Drop the rows of a raw (unsorted) table that are already in full, before any sorting: in
+// late rounds most join output rediscovers known tuples, so the sort then only sees rows
+// that may be new.  The join emits rows grouped by their leading columns, so consecutive
+// probes of the full index touch the same ranges.  Returns the (possibly new) table.
+// The result's columns lie t.n (the unfiltered count) values apart: see `stride`.
+std::pair<DevPtr, TableView> prefilter(Engine& E, const Relation& R, DevPtr buf, TableView t, uint64_t& stride) {
+    stride = t.n;
+    if (R.full[0].n == 0 || t.n == 0) return {buf, t};
+    DevPtr out = E.make(sizeof(uint32_t) * t.arity * t.n);
+    TableView o;
+    memset(&o, 0, sizeof(o));
+    o.arity = t.arity;
+    for (uint32_t c = 0; c < t.arity; c++) o.col[c] = (uint32_t*)out->ptr + (size_t)c * t.n;
+    E.phase_begin(2);
+    o.n = anti_filter(E, t, atom_of(R.full[0]), o);
+    E.phase_end(2);
+    return {out, o};
+}
+
 // a ∪ b of two sorted, duplicate-free indexes (rows may occur in both).
 Index union_sorted(Engine& E, const Index& a, const Index& b) {
     if (a.n == 0) return b;
@@ -396,10 +423,12 @@ Index union_sorted(Engine& E, const Index& a, const Index& b) {
     return u;
 }
 
-// Sort a raw output part, drop duplicates and rows already in full.
+// Drop rows already in full from a raw output part, then sort it and drop duplicates.
 Index reduce_part(Engine& E, Relation& R, DevPtr buf, TableView t) {
-    Index sorted = sort_into_index(E, buf, t, identity_perm(), R.arity);
-    return compute_delta(E, sorted, R.full[0], identity_perm(), R.arity, false);
+    uint64_t stride = 0;
+    auto f = prefilter(E, R, buf, t, stride);
+    Index sorted = sort_into_index(E, f.first, f.second, identity_perm(), R.arity, stride);
+    return compute_delta(E, sorted, empty_index(R.arity, identity_perm()), identity_perm(), R.arity, false);
 }
 
 // Turn one round's join outputs for relation R into its new delta; merge into full.
@@ -408,6 +437,7 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
     JoinOutput& jo = P.out;
     Index newrows = empty_index(R.arity, identity_perm());
     bool known_unique = false;
+    bool filtered = false;   // rows already in full were dropped before sorting
     uint64_t raw = 0;
     for (auto& p : jo.parts) raw += p.n;
     Index d;
@@ -444,9 +474,14 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
         }
         jo.parts.clear();
         jo.owners.clear();
-        newrows = sort_into_index(E, buf, t, identity_perm(), R.arity);
+        uint64_t stride = 0;
+        auto f = prefilter(E, R, buf, t, stride);
+        newrows = sort_into_index(E, f.first, f.second, identity_perm(), R.arity, stride);
+        filtered = true;
     }
-    if (!d.cols && d.n == 0) d = compute_delta(E, newrows, R.full[0], identity_perm(), R.arity, known_unique);
+    if (!d.cols && d.n == 0)
+        d = compute_delta(E, newrows, filtered ? empty_index(R.arity, identity_perm()) : R.full[0], identity_perm(),
+                          R.arity, known_unique);
     jo.parts.clear();
     jo.owners.clear();
     E.delta_rows += d.n;

@@ -164,6 +164,10 @@ void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out);
 // in is sorted; writes the kept rows, in order, to out; returns the count (synchronises).
 uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const TableView& out);
 
+// Keep the rows of in (any order) that are absent from full; order is kept; returns the
+// count (synchronises).
+uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const TableView& out);
+
 // out = merge(a, b) of two sorted, disjoint tables (a.n + b.n rows).
 void merge_rows(Engine& E, const TableView& a, const TableView& b, const TableView& out);
 

@@ -221,6 +221,13 @@ struct UniqueAnti {
     }
 };
 
+// Rows absent from full (the input need not be sorted; order is kept).
+struct AntiOnly {
+    TableView in;
+    AtomView full;
+    __device__ bool operator()(uint64_t i) const { return !contains_row(full, in, i); }
+};
+
 template <class Pred>
 __global__ void k_flag_count(Pred pred, uint64_t n, uint64_t* __restrict__ block_count) {
     const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
@@ -435,6 +442,30 @@ uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const
     if (total) {
         KernelScope ks(E, DL_K_DELTA, 2 * rowb * n + rowb * total);
         k_flag_write<UniqueAnti><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, in, out, cnt.p);
+        DL_CHECK_LAUNCH();
+    }
+    return total;
+}
+
+uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const TableView& out) {
+    const uint64_t n = in.n;
+    if (n == 0) return 0;
+    AntiOnly pred;
+    pred.in = in;
+    pred.full = full;
+    const uint64_t nb = (n + kCompTile - 1) / kCompTile;
+    auto cnt = E.array<uint64_t>(nb + 1);
+    const uint64_t rowb = 4ull * in.arity;
+    {
+        KernelScope ks(E, DL_K_DELTA, rowb * n);
+        k_flag_count<AntiOnly><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, n, cnt.p);
+        DL_CHECK_LAUNCH();
+    }
+    scan_u64(E, cnt.p, nb, false, cnt.p + nb);
+    const uint64_t total = E.readback(cnt.p + nb, 1)[0];
+    if (total) {
+        KernelScope ks(E, DL_K_DELTA, rowb * n + rowb * total);
+        k_flag_write<AntiOnly><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, in, out, cnt.p);
         DL_CHECK_LAUNCH();
     }
     return total;
