@@ -147,7 +147,8 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ key, uint64_t n, uint3
 
 // Stable scatter: warp w of the block owns the contiguous rows [base + w*32*I, base + (w+1)*32*I);
 // iteration j handles row base + w*32*I + j*32 + lane, so (j, lane) order is row order.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(TableView src, TableView dst, int keycol,
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const __grid_constant__ TableView src,
+                                                                const __grid_constant__ TableView dst, int keycol,
                                                                 uint32_t shift, const uint32_t* __restrict__ offs,
                                                                 uint32_t ntiles) {
     __shared__ uint32_t wcnt[kSortWarps][kRadix];
@@ -221,15 +222,66 @@ struct UniqueAnti {
     }
 };
 
-// Rows absent from full (the input need not be sorted; order is kept).
-struct AntiOnly {
-    TableView in;
-    AtomView full;
-    __device__ bool operator()(uint64_t i) const { return !contains_row(full, in, i); }
-};
+// Is row i absent from full?  Called by all 32 lanes of a warp on 32 consecutive rows.  Rows
+// usually arrive grouped by their leading columns (joins emit them in prefix order), so only
+// the first lane of each run of equal leading columns narrows the full index down to that
+// prefix; the rest of the run takes the range by shuffle and searches the last column only.
+__device__ __forceinline__ bool absent_row_warp(const AtomView& full, const TableView& in, uint64_t i, bool valid) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t a = in.arity;
+    bool head = true;
+    if (valid && a > 1 && lane > 0 && i > 0) {
+        head = false;
+        for (uint32_t c = 0; c + 1 < a; c++)
+            if (in.col[c][i] != in.col[c][i - 1]) {
+                head = true;
+                break;
+            }
+    }
+    uint32_t lo = 0, hi = full.n, pok = 1;
+    if (head && valid)
+        for (uint32_t c = 0; c + 1 < a && pok; c++) pok = narrow(full, (int)c, in.col[c][i], lo, hi) ? 1u : 0u;
+    const unsigned heads = __ballot_sync(kFull, head);
+    const int src = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    lo = __shfl_sync(kFull, lo, src);
+    hi = __shfl_sync(kFull, hi, src);
+    pok = __shfl_sync(kFull, pok, src);
+    if (!valid) return false;
+    if (!pok) return true;
+    uint32_t l = lo, h = hi;
+    return !narrow(full, (int)a - 1, in.col[a - 1][i], l, h);
+}
+
+__global__ void k_absent_count(const __grid_constant__ TableView in, const __grid_constant__ AtomView full,
+                               uint64_t* __restrict__ block_count) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    uint64_t c = 0;
+    for (int j = 0; j < kCompItems; j++) {
+        const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+        if (absent_row_warp(full, in, i, i < in.n)) c++;
+    }
+    uint64_t total;
+    block_exclusive_scan(c, total);
+    if (threadIdx.x == 0) block_count[blockIdx.x] = total;
+}
+
+__global__ void k_absent_write(const __grid_constant__ TableView in, const __grid_constant__ AtomView full,
+                               const __grid_constant__ TableView out, const uint64_t* __restrict__ block_off) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    uint64_t run = block_off[blockIdx.x];
+    for (int j = 0; j < kCompItems; j++) {
+        const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+        const uint32_t f = absent_row_warp(full, in, i, i < in.n) ? 1u : 0u;
+        uint32_t total;
+        const uint32_t pos = block_exclusive_scan(f, total);
+        if (f)
+            for (uint32_t c = 0; c < in.arity; c++) out.col[c][run + pos] = in.col[c][i];
+        run += total;
+    }
+}
 
 template <class Pred>
-__global__ void k_flag_count(Pred pred, uint64_t n, uint64_t* __restrict__ block_count) {
+__global__ void k_flag_count(const __grid_constant__ Pred pred, uint64_t n, uint64_t* __restrict__ block_count) {
     const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
     uint64_t c = 0;
     for (int j = threadIdx.x; j < kCompTile; j += blockDim.x) {
@@ -242,7 +294,8 @@ __global__ void k_flag_count(Pred pred, uint64_t n, uint64_t* __restrict__ block
 }
 
 template <class Pred>
-__global__ void k_flag_write(Pred pred, TableView in, TableView out, const uint64_t* __restrict__ block_off) {
+__global__ void k_flag_write(const __grid_constant__ Pred pred, const __grid_constant__ TableView in,
+                             const __grid_constant__ TableView out, const uint64_t* __restrict__ block_off) {
     const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
     uint64_t run = block_off[blockIdx.x];
     for (int j = 0; j < kCompItems; j++) {
@@ -270,7 +323,8 @@ __device__ __forceinline__ bool row_less(const TableView& a, uint64_t i, const T
     return false;
 }
 
-__global__ void k_merge(TableView a, TableView b, TableView out) {
+__global__ void k_merge(const __grid_constant__ TableView a, const __grid_constant__ TableView b,
+                        const __grid_constant__ TableView out) {
     const uint64_t total = a.n + b.n;
     const uint64_t diag = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kMergeItems;
     if (diag >= total) return;
@@ -311,7 +365,7 @@ __global__ void k_column_max(const uint32_t* __restrict__ col, uint64_t n, uint3
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-__global__ void k_digest(TableView t, unsigned long long* d) {
+__global__ void k_digest(const __grid_constant__ TableView t, unsigned long long* d) {
     unsigned long long s = 0, x = 0, c = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < t.n; i += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t h = kTupleHashSeed;
@@ -333,7 +387,7 @@ __global__ void k_digest(TableView t, unsigned long long* d) {
     }
 }
 
-__global__ void k_order_violations(TableView t, unsigned long long* out) {
+__global__ void k_order_violations(const __grid_constant__ TableView t, unsigned long long* out) {
     unsigned long long c = 0;
     for (uint64_t i = 1 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < t.n; i += (uint64_t)gridDim.x * blockDim.x)
         if (!row_less(t, i - 1, t, i)) c++;
@@ -450,22 +504,19 @@ uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const
 uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const TableView& out) {
     const uint64_t n = in.n;
     if (n == 0) return 0;
-    AntiOnly pred;
-    pred.in = in;
-    pred.full = full;
     const uint64_t nb = (n + kCompTile - 1) / kCompTile;
     auto cnt = E.array<uint64_t>(nb + 1);
     const uint64_t rowb = 4ull * in.arity;
     {
         KernelScope ks(E, DL_K_DELTA, rowb * n);
-        k_flag_count<AntiOnly><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, n, cnt.p);
+        k_absent_count<<<(unsigned)nb, kCompThreads, 0, E.stream>>>(in, full, cnt.p);
         DL_CHECK_LAUNCH();
     }
     scan_u64(E, cnt.p, nb, false, cnt.p + nb);
     const uint64_t total = E.readback(cnt.p + nb, 1)[0];
     if (total) {
         KernelScope ks(E, DL_K_DELTA, rowb * n + rowb * total);
-        k_flag_write<AntiOnly><<<(unsigned)nb, kCompThreads, 0, E.stream>>>(pred, in, out, cnt.p);
+        k_absent_write<<<(unsigned)nb, kCompThreads, 0, E.stream>>>(in, full, out, cnt.p);
         DL_CHECK_LAUNCH();
     }
     return total;
