@@ -548,7 +548,8 @@ def main():
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
                "results": {"Tri_rows": int(stats[-1]["join_rows"]), "Q4_rows": int(stats[-1]["count_rows"]),
-                           "rounds": stats[-1]["rounds"], "peak_bytes": int(stats[-1]["peak_bytes"])},
+                           "rounds": stats[-1]["rounds"], "peak_bytes": int(stats[-1]["peak_bytes"]),
+                           "hub_keys": int(stats[-1]["hub_keys"])},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(out))
     eng.close()

@@ -78,6 +78,10 @@ typedef struct dl_config {
     uint64_t chunk_rows;      /* a rule's raw output per round above this many rows is written and
                                  reduced (sorted, deduplicated, anti-joined) in chunks of at most
                                  this size; 0 = default (2^30) */
+    uint32_t hub_rows;        /* a key with at least this many rows in an index that stays fixed
+                                 during dl_fixpoint gets a bitmap of its second-column values, so
+                                 that a join probe into its rows that needs no narrowed range is
+                                 one bit test; 0 = default (2048), UINT32_MAX = never */
 } dl_config;
 
 /* Batched form (dl_config.instances = N >= 1).  The engine holds N independent instances
@@ -211,6 +215,10 @@ typedef struct dl_stats {
     dl_kernel_stat kernels[DL_KERNEL_KINDS];  /* per kernel kind; zero unless DL_FLAG_PROFILE */
     uint32_t top_kind;         /* DL_FLAG_PROFILE: kind of the single longest launch */
     dl_kernel_stat top;        /* that launch (launches = 1) */
+    uint32_t hub_keys;         /* keys given a membership bitmap by the call: index keys with
+                                  >= 2048 rows, so that a join probe into their rows that needs
+                                  no narrowed range is one bit test (implementation detail,
+                                  reported for tests and tuning) */
 } dl_stats;
 
 /* Evaluate all rules to the least fixpoint (semi-naive, Jacobi rounds: every rule of a

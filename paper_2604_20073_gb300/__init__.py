@@ -47,7 +47,7 @@ class dl_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
                 ("alloc", DL_ALLOC_FN), ("free", DL_FREE_FN), ("alloc_user", ctypes.c_void_p),
                 ("flags", ctypes.c_uint32), ("tile_units", ctypes.c_uint32), ("instances", ctypes.c_uint32),
-                ("chunk_rows", ctypes.c_uint64)]
+                ("chunk_rows", ctypes.c_uint64), ("hub_rows", ctypes.c_uint32)]
 
 
 class dl_term(ctypes.Structure):
@@ -70,7 +70,7 @@ class dl_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_join", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("ms_dedup", ctypes.c_double), ("ms_merge", ctypes.c_double),
                 ("kernels", dl_kernel_stat * len(KERNEL_KINDS)), ("top_kind", ctypes.c_uint32),
-                ("top", dl_kernel_stat)]
+                ("top", dl_kernel_stat), ("hub_keys", ctypes.c_uint32)]
 
 
 class dl_server_config(ctypes.Structure):
@@ -192,7 +192,7 @@ class Engine:
     """One engine handle (owns all of its device memory)."""
 
     def __init__(self, device: int = 0, stream=None, arena_bytes: int = 0, flags: int = 0, tile_units: int = 0,
-                 use_torch_allocator: bool = False, instances: int = 0, chunk_rows: int = 0):
+                 use_torch_allocator: bool = False, instances: int = 0, chunk_rows: int = 0, hub_rows: int = 0):
         import torch  # plumbing only: stream handle and (optionally) the caching allocator
         self.lib = load_library()
         if not torch.cuda.is_available():
@@ -209,6 +209,7 @@ class Engine:
         cfg.tile_units = tile_units
         cfg.instances = instances
         cfg.chunk_rows = chunk_rows
+        cfg.hub_rows = hub_rows
         self.instances = instances
         self._cb = None
         if use_torch_allocator:

@@ -117,6 +117,10 @@ AtomView atom_of(const Index& ix) {
     for (uint32_t k = 0; k < ix.arity; k++) a.col[k] = ix.col((int)k);
     a.root = ix.root_ptr();
     a.V = ix.rootV;
+    a.hub = ix.hub ? (const int32_t*)ix.hub->ptr : nullptr;
+    a.bits = ix.bits ? (const uint32_t*)ix.bits->ptr : nullptr;
+    a.bmwords = ix.bmwords;
+    a.hubmin = ix.hubmin;
     a.n = (uint32_t)ix.n;
     a.arity = ix.arity;
     return a;
@@ -174,10 +178,52 @@ Index sort_into_index(Engine& E, DevPtr buf, TableView t, const Perm& perm, uint
 void build_roots(Engine& E, Index& ix, bool needed) {
     ix.root.reset();
     ix.rootV = 0;
+    ix.hub.reset();
+    ix.bits.reset();
+    ix.bmwords = 0;
+    ix.hubmin = 0;
     if (!needed || E.V == 0 || E.V > kDenseRootLimit || ix.n == 0) return;
     ix.root = E.make(sizeof(uint32_t) * ((size_t)E.V + 1));
     ix.rootV = E.V;
     build_root(E, ix.col(0), ix.n, (uint32_t*)ix.root->ptr, E.V);
+}
+
+// Heavy-key bitmaps for an index whose root offsets exist: a join probe into the range of a
+// key with >= E.hub_rows rows becomes one bit test.  Built for indexes that stay fixed while
+// the joins read them (a merge rebuilds the roots and drops the bitmaps).
+void build_hubs(Engine& E, Index& ix) {
+    if (!ix.root || ix.hub || ix.arity != 2 || ix.n < E.hub_rows) return;
+    const uint32_t V = ix.rootV;
+    std::vector<uint32_t> root((size_t)V + 1);
+    DL_CUDA(cudaMemcpyAsync(root.data(), ix.root->ptr, sizeof(uint32_t) * root.size(), cudaMemcpyDeviceToHost,
+                            E.stream));
+    E.sync();
+    std::vector<std::pair<uint32_t, uint32_t>> heavy;   // (degree, key)
+    for (uint32_t k = 0; k < V; k++)
+        if (root[k + 1] - root[k] >= E.hub_rows) heavy.push_back({root[k + 1] - root[k], k});
+    if (heavy.empty()) return;
+    std::sort(heavy.rbegin(), heavy.rend());
+    const uint32_t bmwords = (V + 31) / 32;
+    const uint64_t maxh = kHubBitmapBytes / (4ull * bmwords);
+    if (heavy.size() > maxh) heavy.resize(maxh);
+    if (heavy.empty()) return;
+    std::vector<int32_t> slot(V, -1);
+    std::vector<uint32_t> keys(heavy.size());
+    for (size_t i = 0; i < heavy.size(); i++) {
+        keys[i] = heavy[i].second;
+        slot[heavy[i].second] = (int32_t)i;
+    }
+    ix.hub = E.make(sizeof(int32_t) * V);
+    ix.bits = E.make(sizeof(uint32_t) * (uint64_t)bmwords * keys.size());
+    auto dkeys = E.array<uint32_t>(keys.size());
+    DL_CUDA(cudaMemcpyAsync(ix.hub->ptr, slot.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, E.stream));
+    DL_CUDA(cudaMemcpyAsync(dkeys.p, keys.data(), sizeof(uint32_t) * keys.size(), cudaMemcpyHostToDevice, E.stream));
+    build_hub_bits(E, (const uint32_t*)ix.root->ptr, ix.col(1), dkeys.p, (uint32_t)keys.size(),
+                   (uint32_t*)ix.bits->ptr, bmwords);
+    ix.bmwords = bmwords;
+    ix.hubmin = heavy.back().first;
+    E.hub_keys += keys.size();
+    E.sync();   // the host vectors above must outlive the copies
 }
 
 // Δ = unique(sorted new rows) \ full, written into a fresh index (canonical order).
@@ -563,6 +609,7 @@ void validate_program(Engine& E) {
 void fixpoint(Engine& E, dl_stats* st) {
     auto t0 = std::chrono::steady_clock::now();
     const uint64_t launches0 = E.launches;
+    const uint64_t hub0 = E.hub_keys;
     E.join_rows = E.count_rows = E.delta_rows = 0;
     E.peak = E.used;
     E.event_next = 0;
@@ -598,6 +645,10 @@ void fixpoint(Engine& E, dl_stats* st) {
         std::vector<Variant> round1, rec;
         for (const Rule& r : E.rules) {
             if (E.rels[r.head.rel].stratum != (int)s) continue;
+            for (uint32_t a = 0; a < r.body.size(); a++) {   // indexes fixed during this stratum
+                Relation& B = E.rels[r.body[a].rel];
+                if (B.stratum != (int)s) build_hubs(E, B.full[perm_slot(B, atom_perm(r, a))]);
+            }
             bool is_rec = false;
             for (const RuleAtom& a : r.body) is_rec = is_rec || E.rels[a.rel].stratum == (int)s;
             if (!is_rec) {
@@ -675,6 +726,7 @@ void fixpoint(Engine& E, dl_stats* st) {
         st->delta_rows = E.delta_rows;
         st->peak_bytes = E.peak;
         st->kernel_launches = E.launches - launches0;
+        st->hub_keys = (uint32_t)(E.hub_keys - hub0);
         double* ms[4] = {&st->ms_join, &st->ms_sort, &st->ms_dedup, &st->ms_merge};
         for (int k = 0; k < 4; k++)
             for (auto& pr : E.phases.ev[k]) {
@@ -772,6 +824,7 @@ int dl_engine_create(const dl_config* cfg, dl_engine** out) {
         E->tile_units = c.tile_units ? c.tile_units : 4096;
         E->instances = c.instances;
         if (c.chunk_rows) E->chunk_rows = c.chunk_rows;
+        if (c.hub_rows) E->hub_rows = c.hub_rows;
         if (!E->ualloc) {
             cudaMemPoolProps props;
             memset(&props, 0, sizeof(props));

@@ -69,6 +69,10 @@ struct Index {
     uint64_t cap = 0;
     DevPtr root;                // dense offsets over col[0]: V + 1 uint32 (optional)
     uint32_t rootV = 0;
+    DevPtr hub;                 // int32 per col[0] value: bitmap slot of a heavy key, else -1
+    DevPtr bits;                // per heavy key: bitmap of its col[1] values over [0, V)
+    uint32_t bmwords = 0;       // uint32 words per bitmap (0 = no bitmaps)
+    uint32_t hubmin = 0;        // rows of the lightest key with a bitmap
     uint32_t* col(int k) const { return cols ? (uint32_t*)cols->ptr + (size_t)k * cap : nullptr; }
     const uint32_t* root_ptr() const { return root ? (const uint32_t*)root->ptr : nullptr; }
 };
@@ -78,10 +82,16 @@ struct Index {
 struct AtomView {               // an index as the join kernels see it
     const uint32_t* col[kMaxArity];
     const uint32_t* root;       // dense root offsets or nullptr
+    const int32_t* hub;         // heavy-key bitmap slots or nullptr
+    const uint32_t* bits;
+    uint32_t bmwords;
+    uint32_t hubmin;            // rows of the lightest key with a bitmap
     uint32_t n;
     uint32_t V;
     uint32_t arity;
 };
+constexpr uint32_t kHubMinRows = 2048;            // default: keys with this many rows get a bitmap
+constexpr uint64_t kHubBitmapBytes = 256ull << 20; // bitmap memory per index
 
 struct TableView {              // a plain SoA table (not necessarily sorted)
     uint32_t* col[kMaxArity];
@@ -191,6 +201,11 @@ void mark_runs(Engine& E, const uint32_t* col0, uint64_t n, uint32_t* last, uint
 
 // [lower_bound, upper_bound) of v in the sorted column col0[0..n) (synchronises).
 void find_range(Engine& E, const uint32_t* col0, uint64_t n, uint32_t v, uint64_t* lo, uint64_t* hi);
+
+// Bitmaps of the col[1] values of heavy keys: one block per
+// key in hub_keys, bit v of bitmap slot b set iff (hub_keys[b], v) is a row.
+void build_hub_bits(Engine& E, const uint32_t* col0_root, const uint32_t* col1, const uint32_t* hub_keys,
+                    uint32_t nhubs, uint32_t* bits, uint32_t bmwords);
 
 // Check that rows are strictly increasing; returns number of violations (synchronises).
 uint64_t count_order_violations(Engine& E, const TableView& t);

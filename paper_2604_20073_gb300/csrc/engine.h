@@ -84,6 +84,8 @@ class Engine {
     uint64_t host_scratch[64] = {0};  // readback target (pageable: freeing pinned memory would
                                       // synchronise the whole device, stalling other engines)
     uint64_t launches = 0;
+    uint64_t hub_keys = 0;          // heavy keys given membership bitmaps
+    uint32_t hub_rows = kHubMinRows;  // rows that make a key heavy
     uint64_t join_rows = 0, count_rows = 0, delta_rows = 0;
     bool in_fixpoint = false;
     std::vector<cudaEvent_t> event_pool;

@@ -419,6 +419,16 @@ __global__ void k_find_range(const uint32_t* __restrict__ col0, uint64_t n, uint
     out[1] = lo2;
 }
 
+__global__ void k_hub_bits(const uint32_t* __restrict__ root, const uint32_t* __restrict__ col1,
+                           const uint32_t* __restrict__ hub_keys, uint32_t* __restrict__ bits, uint32_t bmwords) {
+    const uint32_t key = hub_keys[blockIdx.x];
+    uint32_t* bm = bits + (uint64_t)blockIdx.x * bmwords;
+    for (uint32_t r = root[key] + threadIdx.x; r < root[key + 1]; r += blockDim.x) {
+        const uint32_t v = col1[r];
+        atomicOr(bm + (v >> 5), 1u << (v & 31));
+    }
+}
+
 unsigned grid_for(uint64_t n, int threads, unsigned cap = 152u * 16u) {
     uint64_t g = (n + threads - 1) / threads;
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(g, cap));
@@ -587,6 +597,15 @@ void find_range(Engine& E, const uint32_t* col0, uint64_t n, uint32_t v, uint64_
     const uint64_t* h = E.readback(r.p, 2);
     *lo = h[0];
     *hi = h[1];
+}
+
+void build_hub_bits(Engine& E, const uint32_t* root, const uint32_t* col1, const uint32_t* hub_keys,
+                    uint32_t nhubs, uint32_t* bits, uint32_t bmwords) {
+    if (!nhubs) return;
+    DL_CUDA(cudaMemsetAsync(bits, 0, sizeof(uint32_t) * (uint64_t)nhubs * bmwords, E.stream));
+    KernelScope ks(E, DL_K_OTHER, 4ull * nhubs * bmwords);
+    k_hub_bits<<<nhubs, 256, 0, E.stream>>>(root, col1, hub_keys, bits, bmwords);
+    DL_CHECK_LAUNCH();
 }
 
 uint64_t count_order_violations(Engine& E, const TableView& t) {

@@ -49,6 +49,7 @@ struct LevelParams {
     uint8_t src_atom[kMaxSrc + 1];        // atom of each source, kVirtual for the sibling run
     uint8_t src_depth[kMaxSrc + 1];
     uint8_t src_need_range[kMaxSrc + 1];  // 1: the narrowed range is carried to the next level
+    int8_t src_keypos[kMaxSrc + 1];       // depth-1 source: order position of its depth-0 value
     int8_t slot_in[kMaxAtoms];            // frontier slot of each atom's range, -1 = whole index
     int8_t lazy_pos[kMaxAtoms];           // atom whose depth-0 check was deferred: position of that value
     uint64_t nF;
@@ -242,7 +243,7 @@ __device__ __forceinline__ void tile_entries(const LevelParams& P, uint64_t tlo,
     e1 = s_e1;
 }
 
-__global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_count(const __grid_constant__ LevelParams P) {
+__global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count(const __grid_constant__ LevelParams P) {
     uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
     tile_entries(P, tlo, thi, e0, e1);
@@ -368,8 +369,8 @@ struct EntryState {
     const uint32_t* col[NS];
     const uint32_t* root[NS];
     uint32_t rootV[NS];
-    uint32_t lo[NS], hi[NS];
-    const uint32_t* dcol;         // the driver's state (scalars; see Walker-free note below)
+    uint32_t lo[NS], hi[NS];      // lo > hi: col is the bitmap of a heavy key, hi its width in bits
+    const uint32_t* dcol;         // the driver's state (scalars; see the note below)
     const uint32_t* droot;
     uint32_t dlo, dhi, dneed;
     int s0;
@@ -402,6 +403,18 @@ __device__ __forceinline__ void entry_load(const LevelParams& P, EntryState<NS>&
             S.root[s] = dense_root_of(P, s, S.rootV[s]);
             S.lo[s] = lo;
             S.hi[s] = hi;
+            const int a = P.src_atom[s];
+            // a membership-only probe into a heavy key's rows: test its bitmap instead
+            if (a != kVirtual && P.src_depth[s] == 1 && !P.src_need_range[s] && P.atom[a].hub &&
+                hi - lo >= P.atom[a].hubmin) {
+                const uint32_t key = __ldg(P.fval[P.src_keypos[s]] + e);
+                const int32_t slot = key < P.atom[a].V ? __ldg(P.atom[a].hub + key) : -1;
+                if (slot >= 0) {
+                    S.col[s] = P.atom[a].bits + (uint64_t)slot * P.atom[a].bmwords;
+                    S.lo[s] = 0xFFFFFFFFu;
+                    S.hi[s] = P.atom[a].bmwords * 32u;
+                }
+            }
         }
     }
     uint32_t dV;
@@ -436,6 +449,10 @@ __device__ __forceinline__ bool entry_eval(const LevelParams& P, const EntryStat
                 ok = l < h;
                 nlo[s] = l;
                 nhi[s] = h;
+            } else if (S.lo[s] > S.hi[s]) {
+                ok = v < S.hi[s] && ((__ldg(S.col[s] + (v >> 5)) >> (v & 31)) & 1u);   // one bit test
+                nlo[s] = 0;
+                nhi[s] = 0;
             } else {
                 const uint32_t l = lower_bound_u32(S.col[s], S.lo[s], S.hi[s], v);
                 ok = l < S.hi[s] && __ldg(S.col[s] + l) == v;
@@ -776,6 +793,7 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
             P.src_atom[P.nsrc] = (uint8_t)s.atom;
             P.src_depth[P.nsrc] = (uint8_t)s.depth;
             P.src_need_range[P.nsrc] = plan.last_level[s.atom] > (int)lvl ? 1 : 0;
+            P.src_keypos[P.nsrc] = s.depth == 1 ? (int8_t)plan.colpos[s.atom][0] : (int8_t)-1;
             P.nsrc++;
         }
         if (P.nsrc > (uint32_t)kMaxSrc)

@@ -240,3 +240,15 @@ def random_graph(n: int, m: int, seed: int) -> np.ndarray:
     v = _uniform_ids(seed, m, m, n)
     ok = u != v
     return unique_rows(np.stack([u[ok], v[ok]], axis=1))
+
+
+def hub_graph(hubs: int, n: int, m: int, seed: int) -> np.ndarray:
+    """Symmetric graph on n vertices: vertices 0..hubs-1 are adjacent to every other vertex,
+    plus about m uniform random edges among the rest (both directions, no self loops)."""
+    h = np.arange(hubs, dtype=np.uint32)
+    rest = np.arange(hubs, n, dtype=np.uint32)
+    star = np.stack([np.repeat(h, len(rest)), np.tile(rest, hubs)], axis=1)
+    hh = np.array([(a, b) for a in range(hubs) for b in range(hubs) if a != b], dtype=np.uint32).reshape(-1, 2)
+    r = random_graph(n - hubs, m, seed) + np.uint32(hubs)
+    rows = np.concatenate([star, star[:, ::-1], hh, r, r[:, ::-1]])
+    return unique_rows(rows)

@@ -149,6 +149,52 @@ def test_directed_cliques_with_deferred_checks():
     assert len(got["DQ4"]) > 0
 
 
+@pytest.mark.parametrize("hub_rows", [1, 16, 300])
+def test_heavy_key_bitmaps(hub_rows):
+    # probes into keys with >= hub_rows rows test a bitmap of the key's values; the results
+    # must not depend on which keys have one (hub_rows = UINT32_MAX: none)
+    e = dg.hub_graph(3, 420, 1500, 91)
+    rels = {"E": 2, "Tri": 3, "Q4": 4, "Q5": 5}
+    rules = P.TRI + P.Q4 + Q5
+    ref = oracle.evaluate(rels, {"E": e}, rules)
+    d = dg.rmat_edges(1 << 9, 6000, 406)
+    dref = oracle.evaluate({"E": 2, "DQ4": 4}, {"E": d}, DQ4)
+    for order in (["w", "x", "y", "z"], ["z", "y", "x", "w"]):
+        q4 = [(P.Q4[0][0], P.Q4[0][1], order)]
+        got, _, st = gpu(rels, {"E": e}, P.TRI + q4 + Q5, hub_rows=hub_rows)
+        assert st["hub_keys"] > 0
+        for name in ("Tri", "Q4", "Q5"):
+            assert np.array_equal(got[name], ref.relations[name]), (name, order)
+    got, _, st = gpu({"E": 2, "DQ4": 4}, {"E": d}, DQ4, hub_rows=hub_rows, tile_units=64)
+    assert np.array_equal(got["DQ4"], dref.relations["DQ4"])
+    got, _, st = gpu(rels, {"E": e}, rules, hub_rows=0xFFFFFFFF)
+    assert st["hub_keys"] == 0 and np.array_equal(got["Q4"], ref.relations["Q4"])
+
+
+def test_heavy_key_bitmaps_in_recursive_and_random_programs():
+    # a stratum reading relations of lower strata gets bitmaps for them; its own relations
+    # (which change every round) get none
+    rng = np.random.default_rng(77)
+    done = 0
+    for _ in range(40):
+        arity, facts, rules = _random_gpu_program(rng)
+        if not rules:
+            continue
+        got, strata, _ = gpu(arity, facts, rules, hub_rows=2)
+        ref = oracle.evaluate(arity, facts, rules)
+        for name in arity:
+            assert np.array_equal(got[name], ref.relations[name]), name
+        assert sorted(strata) == sorted(ref.strata)
+        done += 1
+    assert done > 25
+    e = dg.hub_graph(2, 300, 600, 5)
+    got, _, st = gpu(P.TC_TRI_RELS, {"E": e}, P.TC_TRI, hub_rows=8)
+    ref = oracle.evaluate(P.TC_TRI_RELS, {"E": e}, P.TC_TRI)
+    assert st["hub_keys"] > 0
+    for name in P.TC_TRI_RELS:
+        assert np.array_equal(got[name], ref.relations[name]), name
+
+
 def test_rerun_is_deterministic_and_debug_checks_pass():
     e = dg.rmat_edges(2048, 16000, 5)
     a = gpu(P.TC_TRI_RELS, {"E": e}, P.TC_TRI, flags=pkg.DL_FLAG_DEBUG_CHECKS)
