@@ -93,6 +93,7 @@ Engine::~Engine() {
 // ------------------------------------------------------------------ indexes
 
 Index make_index(Engine& E, uint32_t arity, const Perm& perm, uint64_t n) {
+    if (n >= 0xFFFFFFFEull) throw Error(DL_ERR_CAPACITY, "index of 2^32 - 2 rows or more");
     Index ix;
     ix.arity = arity;
     for (int k = 0; k < kMaxArity; k++) ix.perm[k] = perm[k];

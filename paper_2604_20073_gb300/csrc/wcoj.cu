@@ -77,6 +77,7 @@ struct LevelParams {
     uint32_t* ohi[kMaxAtoms];
     uint32_t head_arity;
     int8_t head_pos[kMaxArity];           // order position of head column, -1 = constant
+    int8_t head_lvl;                      // MODE_COUNT: the head column holding the level's variable
     uint32_t head_const[kMaxArity];
     uint32_t* ocol[kMaxArity];
     unsigned long long* digest;           // MODE_COUNT: [count, sum, xor]
@@ -363,101 +364,123 @@ __global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_write(const __grid_con
 
 constexpr int kWarps = kJoinThreads / 32;
 
+// How a probe source is searched, packed into its (lo, hi) pair: an ordinary range has
+// lo <= hi < kRootMark (indexes hold fewer than 2^32 - 2 rows).
+constexpr uint32_t kRootMark = 0xFFFFFFFEu;   // col = dense root offsets, hi = their domain size
+constexpr uint32_t kBitsMark = 0xFFFFFFFFu;   // col = a heavy key's bitmap, hi = its width in bits
+
+// An entry's sources with the driver held apart: probe slot k holds source k + (k >= s0).
+// Slots are written and read with compile-time indexes only, so they stay in registers.
 template <int NS>
 struct EntryState {
-    uint64_t e, ebase, eend;
-    const uint32_t* col[NS];
-    const uint32_t* root[NS];
-    uint32_t rootV[NS];
-    uint32_t lo[NS], hi[NS];      // lo > hi: col is the bitmap of a heavy key, hi its width in bits
-    const uint32_t* dcol;         // the driver's state (scalars; see the note below)
-    const uint32_t* droot;
-    uint32_t dlo, dhi, dneed;
+    static constexpr int NP = NS > 1 ? NS - 1 : 1;
+    uint64_t e;
+    uint32_t eoff;                // (warp range start - the entry's first unit) mod 2^32
+    const uint32_t* col[NP];
+    uint32_t lo[NP], hi[NP];
+    const uint32_t* dcol;         // the driver (dlo == kRootMark: iterate the dense domain)
+    uint32_t dlo, dhi;
     int s0;
 };
 
-__device__ __forceinline__ const uint32_t* dense_root_of(const LevelParams& P, int s, uint32_t& V) {
+// Source s's search state for entry e.
+__device__ __forceinline__ const uint32_t* probe_state(const LevelParams& P, int s, uint64_t e, uint32_t& lo,
+                                                       uint32_t& hi) {
     const int a = P.src_atom[s];
-    if (a == kVirtual || P.src_depth[s] != 0 || !P.atom[a].root) {
-        V = 0;
-        return nullptr;
+    if (a != kVirtual && P.src_depth[s] == 0 && P.atom[a].root) {
+        lo = kRootMark;
+        hi = P.atom[a].V;
+        return P.atom[a].root;
     }
-    V = P.atom[a].V;
-    return P.atom[a].root;
+    const uint32_t* col = src_range(P, s, e, lo, hi);
+    // a membership-only probe into a heavy key's rows: test its bitmap instead
+    if (a != kVirtual && P.src_depth[s] == 1 && !P.src_need_range[s] && P.atom[a].hub &&
+        hi - lo >= P.atom[a].hubmin) {
+        const uint32_t key = __ldg(P.fval[P.src_keypos[s]] + e);
+        const int32_t slot = key < P.atom[a].V ? __ldg(P.atom[a].hub + key) : -1;
+        if (slot >= 0) {
+            lo = kBitsMark;
+            hi = P.atom[a].bmwords * 32u;
+            return P.atom[a].bits + (uint64_t)slot * P.atom[a].bmwords;
+        }
+    }
+    return col;
 }
 
-// The driver is addressed through scalars: selecting it from the per-source arrays by the
-// per-entry index s0 would make the compiler index them dynamically and move them out of
-// registers.
+// Loads entry e for a warp whose range starts at unit wlo; returns the entry's end unit.
 template <int NS>
-__device__ __forceinline__ void entry_load(const LevelParams& P, EntryState<NS>& S, uint64_t e) {
+__device__ __forceinline__ uint64_t entry_load(const LevelParams& P, EntryState<NS>& S, uint64_t e, uint64_t wlo) {
     S.e = e;
-    S.ebase = e ? P.C[e - 1] : 0;
-    S.eend = P.C[e];
+    S.eoff = (uint32_t)(wlo - (e ? P.C[e - 1] : 0));
     S.s0 = P.drv[e];
 #pragma unroll
     for (int s = 0; s < NS; s++) {
-        if (s < (int)P.nsrc) {
+        if (s < (int)P.nsrc && s != S.s0) {
             uint32_t lo, hi;
-            S.col[s] = src_range(P, s, e, lo, hi);
-            S.root[s] = dense_root_of(P, s, S.rootV[s]);
-            S.lo[s] = lo;
-            S.hi[s] = hi;
-            const int a = P.src_atom[s];
-            // a membership-only probe into a heavy key's rows: test its bitmap instead
-            if (a != kVirtual && P.src_depth[s] == 1 && !P.src_need_range[s] && P.atom[a].hub &&
-                hi - lo >= P.atom[a].hubmin) {
-                const uint32_t key = __ldg(P.fval[P.src_keypos[s]] + e);
-                const int32_t slot = key < P.atom[a].V ? __ldg(P.atom[a].hub + key) : -1;
-                if (slot >= 0) {
-                    S.col[s] = P.atom[a].bits + (uint64_t)slot * P.atom[a].bmwords;
-                    S.lo[s] = 0xFFFFFFFFu;
-                    S.hi[s] = P.atom[a].bmwords * 32u;
-                }
+            const uint32_t* col = probe_state(P, s, e, lo, hi);
+            constexpr int NP = EntryState<NS>::NP;
+            const int below = s < NP ? s : NP - 1, above = s > 0 ? s - 1 : 0;   // compile-time
+            if (s < S.s0) {
+                S.col[below] = col;
+                S.lo[below] = lo;
+                S.hi[below] = hi;
+            } else {
+                S.col[above] = col;
+                S.lo[above] = lo;
+                S.hi[above] = hi;
             }
         }
     }
-    uint32_t dV;
-    S.dcol = src_range(P, S.s0, e, S.dlo, S.dhi);
-    S.droot = dense_root_of(P, S.s0, dV);
-    S.dneed = P.src_need_range[S.s0];
+    const int a = P.src_atom[S.s0];
+    if (a != kVirtual && P.src_depth[S.s0] == 0 && P.atom[a].root) {
+        S.dcol = P.atom[a].root;
+        S.dlo = kRootMark;
+        S.dhi = P.atom[a].V;
+    } else {
+        S.dcol = src_range(P, S.s0, e, S.dlo, S.dhi);
+    }
+    return P.C[e];
 }
 
+// The entry's unit `local` (counted from its first unit): the candidate value v and whether
+// every probe source holds it.  nlo/nhi (probe slots) and dnlo/dnhi (driver) receive the
+// narrowed ranges.
 template <int NS>
-__device__ __forceinline__ bool entry_eval(const LevelParams& P, const EntryState<NS>& S, uint64_t u, uint32_t& v,
-                                           uint32_t (&nlo)[NS], uint32_t (&nhi)[NS], uint32_t& dnlo, uint32_t& dnhi) {
-    const uint64_t local = u - S.ebase;
+__device__ __forceinline__ bool entry_eval(const LevelParams& P, const EntryState<NS>& S, uint32_t local,
+                                           uint32_t& v, uint32_t (&nlo)[EntryState<NS>::NP],
+                                           uint32_t (&nhi)[EntryState<NS>::NP], uint32_t& dnlo, uint32_t& dnhi) {
     bool ok;
-    if (S.droot) {
-        v = (uint32_t)local;                       // iterate the dense value domain
-        dnlo = __ldg(S.droot + v);
-        dnhi = __ldg(S.droot + v + 1);
+    if (S.dlo == kRootMark) {
+        v = local;                                 // iterate the dense value domain
+        dnlo = __ldg(S.dcol + v);
+        dnhi = __ldg(S.dcol + v + 1);
         ok = dnlo < dnhi;
     } else {
-        const uint32_t r = S.dlo + (uint32_t)local;
+        const uint32_t r = S.dlo + local;
         v = __ldg(S.dcol + r);
         ok = !(r > S.dlo && __ldg(S.dcol + r - 1) == v);   // only the first row of a value
         dnlo = r;
-        dnhi = (ok && S.dneed) ? upper_bound_u32(S.dcol, r + 1, S.dhi, v) : r + 1;
+        dnhi = (ok && P.src_need_range[S.s0]) ? upper_bound_u32(S.dcol, r + 1, S.dhi, v) : r + 1;
     }
 #pragma unroll
-    for (int s = 0; s < NS; s++) {
-        if (ok && s < (int)P.nsrc && s != S.s0) {
-            if (S.root[s]) {
-                const uint32_t l = v < S.rootV[s] ? __ldg(S.root[s] + v) : 0;
-                const uint32_t h = v < S.rootV[s] ? __ldg(S.root[s] + v + 1) : 0;
+    for (int k = 0; k < NS - 1; k++) {
+        if (ok && k + 1 < (int)P.nsrc) {
+            if (S.lo[k] == kRootMark) {
+                const uint32_t l = v < S.hi[k] ? __ldg(S.col[k] + v) : 0;
+                const uint32_t h = v < S.hi[k] ? __ldg(S.col[k] + v + 1) : 0;
                 ok = l < h;
-                nlo[s] = l;
-                nhi[s] = h;
-            } else if (S.lo[s] > S.hi[s]) {
-                ok = v < S.hi[s] && ((__ldg(S.col[s] + (v >> 5)) >> (v & 31)) & 1u);   // one bit test
-                nlo[s] = 0;
-                nhi[s] = 0;
+                nlo[k] = l;
+                nhi[k] = h;
+            } else if (S.lo[k] == kBitsMark) {
+                ok = v < S.hi[k] && ((__ldg(S.col[k] + (v >> 5)) >> (v & 31)) & 1u);   // one bit test
+                nlo[k] = 0;
+                nhi[k] = 0;
             } else {
-                const uint32_t l = lower_bound_u32(S.col[s], S.lo[s], S.hi[s], v);
-                ok = l < S.hi[s] && __ldg(S.col[s] + l) == v;
-                nlo[s] = l;
-                nhi[s] = (ok && P.src_need_range[s]) ? upper_bound_u32(S.col[s], l + 1, S.hi[s], v) : l + 1;
+                const uint32_t l = lower_bound_u32(S.col[k], S.lo[k], S.hi[k], v);
+                ok = l < S.hi[k] && __ldg(S.col[k] + l) == v;
+                nlo[k] = l;
+                const int q = k + (k >= S.s0 ? 1 : 0);
+                nhi[k] = (ok && P.src_need_range[q]) ? upper_bound_u32(S.col[k], l + 1, S.hi[k], v) : l + 1;
             }
         }
     }
@@ -472,39 +495,48 @@ __device__ __forceinline__ void warp_range(const LevelParams& P, uint64_t& wlo, 
     whi = min(wlo + per, thi);
 }
 
+// Value of head column c (not the level's variable) for frontier entry e.
+__device__ __forceinline__ uint32_t head_value(const LevelParams& P, int c, uint64_t e) {
+    const int pos = P.head_pos[c];
+    return pos < 0 ? P.head_const[c] : __ldg(P.fval[pos] + e);
+}
+
 template <int NS>
 __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm(const __grid_constant__ LevelParams P) {
     const int lane = threadIdx.x & 31;
     uint64_t wlo, whi;
     warp_range(P, wlo, whi);
-    unsigned long long cnt = 0, hs = 0, hx = 0;
+    uint32_t cnt = 0;
+    unsigned long long hs = 0, hx = 0;
     if (wlo < whi) {
+        // unit positions below are relative to wlo (a warp range spans fewer than 2^32 units)
+        const uint32_t span = (uint32_t)(whi - wlo);
         uint64_t e = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, wlo);
         EntryState<NS> S;
-        uint64_t u = wlo;
+        uint32_t r = 0;
+        uint64_t hpre = 0;        // MODE_COUNT: row hash over the head columns before head_lvl
         for (;;) {
-            entry_load(P, S, e);
-            const uint64_t stop = min(S.eend, whi);
-            for (uint64_t base = u; base < stop; base += 32) {
-                const uint64_t uu = base + lane;
-                uint32_t v, nlo[NS], nhi[NS], dnlo, dnhi;
-                if (uu >= stop || !entry_eval(P, S, uu, v, nlo, nhi, dnlo, dnhi)) continue;
+            const uint32_t stop = (uint32_t)(min(entry_load(P, S, e, wlo), whi) - wlo);
+            if (P.mode == MODE_COUNT) {
+                hpre = kTupleHashSeed;
+                for (int c = 0; c < P.head_lvl; c++) hpre = tuple_hash_step(hpre, head_value(P, c, e), c);
+            }
+            for (uint32_t b = r; b < stop; b += 32) {
+                const uint32_t rr = b + lane;
+                uint32_t v, nlo[EntryState<NS>::NP], nhi[EntryState<NS>::NP], dnlo, dnhi;
+                if (rr >= stop || !entry_eval(P, S, rr + S.eoff, v, nlo, nhi, dnlo, dnhi)) continue;
                 cnt++;
                 if (P.mode == MODE_COUNT) {
-                    uint64_t h = kTupleHashSeed;
-                    for (uint32_t c = 0; c < P.head_arity; c++) {
-                        const int pos = P.head_pos[c];
-                        const uint32_t x = pos < 0 ? P.head_const[c] : (pos == (int)P.level ? v : __ldg(P.fval[pos] + e));
-                        h = tuple_hash_step(h, x, c);
-                    }
+                    uint64_t h = tuple_hash_step(hpre, v, P.head_lvl);
+                    for (uint32_t c = P.head_lvl + 1; c < P.head_arity; c++) h = tuple_hash_step(h, head_value(P, c, e), c);
                     hs += h;
                     hx ^= h;
                 }
             }
-            u = stop;
-            if (u >= whi) break;
+            r = stop;
+            if (r >= span) break;
             e++;
-            while (P.C[e] <= u) e++;   // entries without units
+            while (P.C[e] <= wlo + r) e++;   // entries without units
         }
     }
 #pragma unroll
@@ -516,7 +548,7 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
     if (lane == 0) {
         P.block_count[(uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)] = cnt;
         if (P.mode == MODE_COUNT && cnt) {
-            atomicAdd(&P.digest[0], cnt);
+            atomicAdd(&P.digest[0], (unsigned long long)cnt);
             atomicAdd(&P.digest[1], hs);
             atomicXor(&P.digest[2], hx);
         }
@@ -532,15 +564,15 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 5 : 4) k_wcoj_write_wm
     uint64_t o = P.block_count[(P.tile_base + blockIdx.x) * kWarps + (threadIdx.x >> 5)] - P.out_base;
     uint64_t e = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, wlo);
     EntryState<NS> S;
-    uint64_t u = wlo;
+    const uint32_t span = (uint32_t)(whi - wlo);   // unit positions relative to wlo
+    uint32_t r = 0;
     const unsigned lt = (1u << lane) - 1;
     for (;;) {
-        entry_load(P, S, e);
-        const uint64_t stop = min(S.eend, whi);
-        for (uint64_t base = u; base < stop; base += 32) {
-            const uint64_t uu = base + lane;
-            uint32_t v = 0, nlo[NS], nhi[NS], dnlo = 0, dnhi = 0;
-            const bool f = uu < stop && entry_eval(P, S, uu, v, nlo, nhi, dnlo, dnhi);
+        const uint32_t stop = (uint32_t)(min(entry_load(P, S, e, wlo), whi) - wlo);
+        for (uint32_t b = r; b < stop; b += 32) {
+            const uint32_t rr = b + lane;
+            uint32_t v = 0, nlo[EntryState<NS>::NP], nhi[EntryState<NS>::NP], dnlo = 0, dnhi = 0;
+            const bool f = rr < stop && entry_eval(P, S, rr + S.eoff, v, nlo, nhi, dnlo, dnhi);
             const unsigned ball = __ballot_sync(kFull, f);
             if (f) {
                 const uint64_t w = o + __popc(ball & lt);
@@ -565,22 +597,23 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 5 : 4) k_wcoj_write_wm
                         }
                     }
 #pragma unroll
-                    for (int q = 0; q < NS; q++) {
-                        if (q >= (int)P.nsrc || q == S.s0) continue;
+                    for (int k = 0; k < NS - 1; k++) {
+                        if (k + 1 >= (int)P.nsrc) continue;
+                        const int q = k + (k >= S.s0 ? 1 : 0);   // the probe slot's source
                         for (uint32_t c = 0; c < P.ncarry; c++)
                             if (P.carry_src[c] == q) {
-                                P.olo[c][w] = nlo[q];
-                                P.ohi[c][w] = nhi[q];
+                                P.olo[c][w] = nlo[k];
+                                P.ohi[c][w] = nhi[k];
                             }
                     }
                 }
             }
             o += __popc(ball);
         }
-        u = stop;
-        if (u >= whi) break;
+        r = stop;
+        if (r >= span) break;
         e++;
-        while (P.C[e] <= u) e++;
+        while (P.C[e] <= wlo + r) e++;
     }
 }
 
@@ -859,6 +892,10 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
             DL_CUDA(cudaMemsetAsync(dg.p, 0, 24, E.stream));
             P.mode = MODE_COUNT;
             P.digest = (unsigned long long*)dg.p;
+            P.head_lvl = -1;
+            for (uint32_t c = 0; c < P.head_arity; c++)
+                if (P.head_pos[c] == (int)lvl) P.head_lvl = (int8_t)c;
+            if (P.head_lvl < 0) throw Error(DL_ERR_STATE, "count sink head lacks the last variable");
             {
                 KernelScope ks(E, DL_K_JOIN_COUNT, 4 * T + (entry_bytes + 9) * nF);
                 launch_count();
