@@ -81,7 +81,8 @@ typedef struct dl_config {
     uint32_t hub_rows;        /* a key with at least this many rows in an index that stays fixed
                                  during dl_fixpoint gets a bitmap of its second-column values, so
                                  that a join probe into its rows that needs no narrowed range is
-                                 one bit test; 0 = default (2048), UINT32_MAX = never */
+                                 one bit test; 0 = default (512), UINT32_MAX = never.  Bitmaps
+                                 take at most 1 GiB per index and a quarter of the budget left */
 } dl_config;
 
 /* Batched form (dl_config.instances = N >= 1).  The engine holds N independent instances
@@ -216,7 +217,7 @@ typedef struct dl_stats {
     uint32_t top_kind;         /* DL_FLAG_PROFILE: kind of the single longest launch */
     dl_kernel_stat top;        /* that launch (launches = 1) */
     uint32_t hub_keys;         /* keys given a membership bitmap by the call: index keys with
-                                  >= 2048 rows, so that a join probe into their rows that needs
+                                  >= dl_config.hub_rows rows, so that a join probe into them that needs
                                   no narrowed range is one bit test (implementation detail,
                                   reported for tests and tuning) */
 } dl_stats;

@@ -205,7 +205,11 @@ void build_hubs(Engine& E, Index& ix) {
     if (heavy.empty()) return;
     std::sort(heavy.rbegin(), heavy.rend());
     const uint32_t bmwords = (V + 31) / 32;
-    const uint64_t maxh = kHubBitmapBytes / (4ull * bmwords);
+    // at most kHubBitmapBytes, and at most a quarter of the budget left: the bitmaps only
+    // speed probes up and must not turn a program that fits into one that does not
+    const uint64_t room = std::min<uint64_t>(kHubBitmapBytes, E.budget > E.used ? (E.budget - E.used) / 4 : 0);
+    const uint64_t slots = sizeof(int32_t) * (uint64_t)V;
+    const uint64_t maxh = room > slots ? (room - slots) / (sizeof(uint32_t) * (uint64_t)bmwords) : 0;
     if (heavy.size() > maxh) heavy.resize(maxh);
     if (heavy.empty()) return;
     std::vector<int32_t> slot(V, -1);

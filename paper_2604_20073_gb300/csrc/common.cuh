@@ -90,8 +90,8 @@ struct AtomView {               // an index as the join kernels see it
     uint32_t V;
     uint32_t arity;
 };
-constexpr uint32_t kHubMinRows = 2048;            // default: keys with this many rows get a bitmap
-constexpr uint64_t kHubBitmapBytes = 4096ull << 20; // bitmap memory per index
+constexpr uint32_t kHubMinRows = 512;              // default: keys with this many rows get a bitmap
+constexpr uint64_t kHubBitmapBytes = 1024ull << 20; // bitmap memory per index (at most)
 
 struct TableView {              // a plain SoA table (not necessarily sorted)
     uint32_t* col[kMaxArity];

@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
 }
 
 template <int NS>
-__global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 5 : 4) k_wcoj_write_wm(const __grid_constant__ LevelParams P) {
+__global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 6 : 4) k_wcoj_write_wm(const __grid_constant__ LevelParams P) {
     const int lane = threadIdx.x & 31;
     uint64_t wlo, whi;
     warp_range(P, wlo, whi);
