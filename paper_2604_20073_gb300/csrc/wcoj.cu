@@ -458,9 +458,13 @@ __device__ __forceinline__ bool entry_eval(const LevelParams& P, const EntryStat
     } else {
         const uint32_t r = S.dlo + local;
         v = __ldg(S.dcol + r);
-        ok = !(r > S.dlo && __ldg(S.dcol + r - 1) == v);   // only the first row of a value
+        // A driver whose atom has later columns repeats a value over that value's rows: only
+        // the first row of a value is a candidate.  Otherwise (the atom's last column under a
+        // bound prefix, or a sibling run) the values are distinct.
+        const bool need = P.src_need_range[S.s0];
+        ok = !(need && r > S.dlo && __ldg(S.dcol + r - 1) == v);
         dnlo = r;
-        dnhi = (ok && P.src_need_range[S.s0]) ? upper_bound_u32(S.dcol, r + 1, S.dhi, v) : r + 1;
+        dnhi = (ok && need) ? upper_bound_u32(S.dcol, r + 1, S.dhi, v) : r + 1;
     }
 #pragma unroll
     for (int k = 0; k < NS - 1; k++) {
@@ -504,18 +508,27 @@ __device__ __forceinline__ uint32_t head_value(const LevelParams& P, int c, uint
 template <int NS>
 __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm(const __grid_constant__ LevelParams P) {
     const int lane = threadIdx.x & 31;
-    uint64_t wlo, whi;
-    warp_range(P, wlo, whi);
+    // the warp's range lives in shared memory between entries (registers are the limit here)
+    __shared__ unsigned long long s_wlo[kWarps], s_whi[kWarps];
+    {
+        uint64_t wlo, whi;
+        warp_range(P, wlo, whi);
+        if (lane == 0) {
+            s_wlo[threadIdx.x >> 5] = wlo;
+            s_whi[threadIdx.x >> 5] = whi;
+        }
+        __syncwarp();
+    }
     uint32_t cnt = 0;
     unsigned long long hs = 0, hx = 0;
-    if (wlo < whi) {
+    if (s_wlo[threadIdx.x >> 5] < s_whi[threadIdx.x >> 5]) {
         // unit positions below are relative to wlo (a warp range spans fewer than 2^32 units)
-        const uint32_t span = (uint32_t)(whi - wlo);
-        uint64_t e = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, wlo);
+        uint64_t e = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, s_wlo[threadIdx.x >> 5]);
         EntryState<NS> S;
         uint32_t r = 0;
         uint64_t hpre = 0;        // MODE_COUNT: row hash over the head columns before head_lvl
         for (;;) {
+            const uint64_t wlo = s_wlo[threadIdx.x >> 5], whi = s_whi[threadIdx.x >> 5];
             const uint32_t stop = (uint32_t)(min(entry_load(P, S, e, wlo), whi) - wlo);
             if (P.mode == MODE_COUNT) {
                 hpre = kTupleHashSeed;
@@ -534,9 +547,10 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
                 }
             }
             r = stop;
-            if (r >= span) break;
+            const uint64_t at = s_wlo[threadIdx.x >> 5] + r;
+            if (at >= s_whi[threadIdx.x >> 5]) break;
             e++;
-            while (P.C[e] <= wlo + r) e++;   // entries without units
+            while (P.C[e] <= at) e++;   // entries without units
         }
     }
 #pragma unroll
