@@ -73,7 +73,9 @@ typedef struct dl_config {
     dl_free_fn free;
     void* alloc_user;
     uint32_t flags;           /* DL_FLAG_* */
-    uint32_t tile_units;      /* join work units per CTA tile; 0 = default (4096) */
+    uint32_t tile_units;      /* join work units per CTA tile; 0 = chosen per join level: the
+                                 largest power of two in [4096, 2^16] that still leaves eight
+                                 waves of resident CTAs */
     uint32_t instances;       /* 0: one program.  N >= 1: batched form, see below */
     uint64_t chunk_rows;      /* a rule's raw output per round above this many rows is written and
                                  reduced (sorted, deduplicated, anti-joined) in chunks of at most

@@ -826,7 +826,10 @@ int dl_engine_create(const dl_config* cfg, dl_engine** out) {
         E->ufree = c.free;
         E->uuser = c.alloc_user;
         E->flags = c.flags;
-        E->tile_units = c.tile_units ? c.tile_units : 4096;
+        E->tile_units = c.tile_units;
+        int sms = 0;
+        DL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device));
+        E->sms = (uint32_t)std::max(sms, 1);
         E->instances = c.instances;
         if (c.chunk_rows) E->chunk_rows = c.chunk_rows;
         if (c.hub_rows) E->hub_rows = c.hub_rows;

@@ -72,7 +72,8 @@ class Engine {
     dl_free_fn ufree = nullptr;
     void* uuser = nullptr;
     uint32_t flags = 0;
-    uint32_t tile_units = 4096;
+    uint32_t tile_units = 0;        // 0: chosen per join level (auto_tile)
+    uint32_t sms = 152;             // multiprocessors of the device
     std::string err;
     std::vector<Relation> rels;
     std::vector<Rule> rules;

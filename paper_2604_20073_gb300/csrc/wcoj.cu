@@ -744,6 +744,16 @@ Plan make_plan(const Rule& R, const std::vector<const Index*>& idx) {
     return p;
 }
 
+// Units per CTA tile for a level of T units.  Each warp starts with a search for its first
+// entry, which larger tiles amortise; at least eight waves of resident CTAs (8 per SM) keep
+// the tail of the launch short.
+uint32_t auto_tile(const Engine& E, uint64_t T) {
+    const uint64_t waves = 8ull * 8ull * E.sms;
+    uint32_t t = 4096;
+    while (t < (1u << 16) && T / (2ull * t) >= waves) t *= 2;
+    return t;
+}
+
 void launch_seg(Engine& E, const uint32_t* parent, uint64_t n, uint32_t* seg, uint32_t* segstart) {
     const unsigned g = (unsigned)((n + 255) / 256);
     {
@@ -885,6 +895,7 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
         const uint64_t T = E.readback(C.p + nF, 1)[0];
         if (T == 0) { E.phase_end(0); return; }
         P.T = T;
+        P.tile = E.tile_units ? E.tile_units : auto_tile(E, T);
         const uint64_t ntiles = P.naive ? nF : (T + P.tile - 1) / P.tile;
         if (ntiles >= (1ull << 31)) throw Error(DL_ERR_CAPACITY, "join level exceeds 2^31 tiles");
         // warp-major kernels when entries average >= 32 units (one count per warp)
