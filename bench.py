@@ -122,16 +122,17 @@ class Clocks:
 
 
 def traffic_for(kernel_kind):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the
-    kernel's source has not changed since the counters were taken."""
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if none
+    of the sources it depends on has changed since the counters were taken."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(p))
         ent = d[kernel_kind]
-        src = open(os.path.join(ROOT, "paper_2604_20073_gb300", "csrc", ent["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != ent["source_sha256"]:
-            return None
+        for name, sha in ent["sources_sha256"].items():
+            src = open(os.path.join(ROOT, "paper_2604_20073_gb300", "csrc", name), "rb").read()
+            if hashlib.sha256(src).hexdigest() != sha:
+                return None
         return ent["dram_bytes_per_launch_fullsize"]
     except Exception:
         return None
