@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="cyclic", choices=["cyclic", "batched", "served"],
+    ap.add_argument("--workload", default="cyclic", choices=["cyclic", "batched", "served", "split"],
                     help="cyclic: the Tri + Q4 fixpoint line (default); batched: 4096 TC+Tri instances; "
-                         "served: Poisson request mix through the serving loop")
+                         "served: Poisson request mix through the serving loop; split: helper-relation "
+                         "splitting ablation on CallGraphEdge")
+    ap.add_argument("--cge-scale", type=float, default=20.0)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--instances", type=int, default=4096)
     return ap.parse_args()
@@ -447,10 +449,77 @@ def run_served_workload(args):
     print(json.dumps(out))
 
 
+def run_split_workload(args):
+    """Helper-relation splitting ablation (Section 5, CallGraphEdge): the six-atom rule as one
+    eight-level join vs split into HelpNT(sn, dsc, h, m) <- HeapAllocationType, MethodLookup
+    and a five-atom consumer; each with the balanced histogram assignment and with one
+    frontier entry per CTA (DL_FLAG_NAIVE_ROOTS).  Facts: call_graph_facts at --cge-scale."""
+    import numpy as np
+    import torch
+
+    import paper_2604_20073_gb300 as pkg
+    from paper_2604_20073_gb300 import datagen as dg
+    CGE_RELS = {"Reachable": 1, "InstructionMethod": 2, "VirtualMethodInvoc": 4, "VarPointsTo": 2,
+                "HeapAllocationType": 2, "MethodLookup": 4, "CallGraphEdge": 2}
+    head, body, order = (("CallGraphEdge", ["i", "m"]),
+                         [("Reachable", ["j"]), ("InstructionMethod", ["i", "j"]),
+                          ("VirtualMethodInvoc", ["i", "b", "sn", "dsc"]), ("VarPointsTo", ["h", "b"]),
+                          ("HeapAllocationType", ["h", "t"]), ("MethodLookup", ["sn", "dsc", "t", "m"])],
+                         ["j", "i", "b", "sn", "dsc", "h", "t", "m"])
+    facts = dg.call_graph_facts(args.cge_scale, 1005)
+    stream = torch.cuda.current_stream()
+    res, outs = {}, {}
+    clocks = Clocks(0)
+    for split in (False, True):
+        for naive in (False, True):
+            eng = pkg.Engine(flags=pkg.DL_FLAG_PROFILE | (pkg.DL_FLAG_NAIVE_ROOTS if naive else 0))
+            for name, a in CGE_RELS.items():
+                eng.relation(name, a)
+            if split:
+                eng.rule_split(head, body, order, (4, 5), "HelpNT")
+            else:
+                eng.rule(head, body, order)
+            for name, rows in facts.items():
+                eng.load(name, rows)
+            times, st = [], None
+            for k in range(args.warmup + args.steps):
+                eng.clear("CallGraphEdge")
+                if split:
+                    eng.clear("HelpNT")
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                st = eng.fixpoint()
+                b.record(stream)
+                torch.cuda.synchronize()
+                if k >= args.warmup:
+                    times.append(a.elapsed_time(b))
+            key = ("split" if split else "monolithic") + ("_naive_roots" if naive else "_balanced")
+            res[key] = {"ms": statistics.mean(times), "join_rows": int(st["join_rows"]),
+                        "helper_rows": int(eng.size("HelpNT")) if split else 0,
+                        "kernels_ms": {k: round(v["ms"], 2) for k, v in st["kernels"].items() if v["launches"]}}
+            outs[key] = eng.fetch("CallGraphEdge")
+            eng.close()
+    clk = clocks.stop()
+    ref = outs["monolithic_balanced"]
+    same = all(np.array_equal(o, ref) for o in outs.values())
+    print(json.dumps({"metric": "fixpoint s (CallGraphEdge: one 8-level join vs helper split, balanced vs naive roots)",
+                      "value": res["monolithic_balanced"]["ms"] / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": res["monolithic_balanced"]["ms"],
+                      "higher_is_better": False, "dtype": "u32", "data": "synthetic",
+                      "config": {"workload": "CallGraphEdge (virtual-call resolution), call_graph_facts",
+                                 "scale": args.cge_scale, "seed": 1005,
+                                 "facts": {k: int(len(v)) for k, v in facts.items()}},
+                      "ablation": res, "CallGraphEdge_rows": int(len(ref)), "identical_results": same,
+                      "clocks": clk}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "split":
+        return run_split_workload(args)
     if args.workload == "batched":
         return run_batched_workload(args)
     if args.workload == "served":

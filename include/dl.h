@@ -181,6 +181,33 @@ typedef struct dl_atom {
 int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody,
                 const uint32_t* var_order, uint32_t nvars, dl_rule_id* out);
 
+/* Helper-relation splitting (Section 5, the CallGraphEdge example): add a rule in two parts.
+ * The body atoms selected by `mask` (bit b = body[b]) are factored out into a helper rule
+ *     helper_name(c1, ..., ck) <- the selected atoms
+ * and the rest becomes the consumer rule
+ *     head <- the other atoms, helper_name(c1, ..., ck),
+ * where c1..ck are the variables the selected atoms share with the other atoms or the head,
+ * in var_order's order (dl_split_columns returns them).  Each part's variable order is
+ * var_order restricted to its body's variables.  A new relation helper_name of arity k is
+ * created.  The split changes no result: the consumer's bindings are exactly the original
+ * rule's, projected through the helper.  It moves skewed inner variables of a deep rule to
+ * the top levels of two shallower joins, where the histogram balancing reaches them.  Round
+ * counts are unchanged when the selected atoms read only relations of lower strata; when a
+ * selected atom is recursive, the helper joins the recursive stratum and derived tuples may
+ * take extra rounds.
+ * Errors: everything dl_rule_add reports for the unsplit rule; DL_ERR_ARG (mask empty, all
+ * atoms, or beyond nbody; empty or duplicate helper_name); DL_ERR_UNSUPPORTED (the selected
+ * atoms share no variable with the rest, or k > DL_MAX_ARITY).  On error nothing is added. */
+int dl_rule_add_split(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody,
+                      const uint32_t* var_order, uint32_t nvars, uint64_t mask, const char* helper_name,
+                      dl_rel_id* helper_rel, dl_rule_id* helper_rule, dl_rule_id* consumer_rule);
+
+/* The helper columns dl_rule_add_split would create (host only; needs no engine or GPU):
+ * *ncols receives k; cols (may be NULL) receives the k variable ids if cap >= k, else
+ * DL_ERR_ARG.  Errors as dl_rule_add_split for the mask; the rule itself is not checked. */
+int dl_split_columns(const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,
+                     uint32_t nvars, uint64_t mask, uint32_t* cols, uint32_t cap, uint32_t* ncols);
+
 /* ------------------------------------------------------------------ fixpoint */
 
 /* Kernel kinds reported in dl_stats.kernels (filled when DL_FLAG_PROFILE is set). */

@@ -120,6 +120,11 @@ _SIGS = {
     "dl_relation_clear": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "dl_rule_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_atom), ctypes.POINTER(dl_atom),
                                    ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p]),
+    "dl_rule_add_split": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_atom), ctypes.POINTER(dl_atom),
+                                         ctypes.c_uint32, _u32p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_char_p,
+                                         _u32p, _u32p, _u32p]),
+    "dl_split_columns": (ctypes.c_int, [ctypes.POINTER(dl_atom), ctypes.POINTER(dl_atom), ctypes.c_uint32, _u32p,
+                                        ctypes.c_uint32, ctypes.c_uint64, _u32p, ctypes.c_uint32, _u32p]),
     "dl_fixpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_stats)]),
     "dl_stratum_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p, _u32p]),
     "dl_relation_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u64p]),
@@ -325,6 +330,32 @@ class Engine:
                                          ctypes.byref(rid)))
         return rid.value
 
+    def rule_split(self, head, body, order, factored, helper: str):
+        """Add a rule split in two (dl_rule_add_split): the body atoms at the positions in
+        `factored` go into a helper rule whose head is relation `helper`; returns
+        (helper columns as variable names, helper rule id, consumer rule id)."""
+        var_ids: dict = {}
+        keep: list = []
+        batoms = (dl_atom * len(body))()
+        for i, b in enumerate(body):
+            batoms[i] = self._atom(b, var_ids, keep)
+        h = self._atom(head, var_ids, keep)
+        ordr = (ctypes.c_uint32 * len(order))(*[var_ids.get(v, 1023) for v in order])
+        mask = sum(1 << i for i in set(factored))
+        cols = (ctypes.c_uint32 * 8)()
+        k = ctypes.c_uint32()
+        rc = self.lib.dl_split_columns(ctypes.byref(h), batoms, len(body), ordr, len(order), mask, cols, 8,
+                                       ctypes.byref(k))
+        hrel, hr, cr = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        self._check(self.lib.dl_rule_add_split(self.h, ctypes.byref(h), batoms, len(body), ordr, len(order), mask,
+                                               helper.encode(), ctypes.byref(hrel), ctypes.byref(hr), ctypes.byref(cr)))
+        assert rc == DL_OK
+        names = {v: n for n, v in var_ids.items()}
+        self.rel_ids[helper] = hrel.value
+        self.arity[helper] = k.value
+        self.names.append(helper)
+        return [names[c] for c in cols[: k.value]], hr.value, cr.value
+
     def fixpoint(self) -> dict:
         st = dl_stats()
         self._check(self.lib.dl_fixpoint(self.h, ctypes.byref(st)))
@@ -509,6 +540,40 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def split_columns(head, body, order, factored) -> list:
+    """The helper columns (variable names) that splitting `factored` out of the rule would
+    create (dl_split_columns; host only, no GPU needed).  Raises DatalogError on a bad split."""
+    lib = load_library()
+    var_ids: dict = {}
+    keep: list = []
+
+    def atom(a):
+        rel, terms = a
+        ts = (dl_term * len(terms))()
+        for i, t in enumerate(terms):
+            if isinstance(t, str):
+                ts[i].kind, ts[i].id = DL_TERM_VAR, var_ids.setdefault(t, len(var_ids))
+            else:
+                ts[i].kind, ts[i].id = DL_TERM_CONST, int(t)
+        keep.append(ts)
+        x = dl_atom()
+        x.rel, x.arity, x.terms = 0, len(terms), ts
+        return x
+    batoms = (dl_atom * len(body))()
+    for i, b in enumerate(body):
+        batoms[i] = atom(b)
+    h = atom(head)
+    ordr = (ctypes.c_uint32 * len(order))(*[var_ids.get(v, 1023) for v in order])
+    cols = (ctypes.c_uint32 * 16)()
+    k = ctypes.c_uint32()
+    rc = lib.dl_split_columns(ctypes.byref(h), batoms, len(body), ordr, len(order),
+                              sum(1 << i for i in set(factored)), cols, 16, ctypes.byref(k))
+    if rc != DL_OK:
+        raise DatalogError(rc, "dl_split_columns failed")
+    names = {v: n for n, v in var_ids.items()}
+    return [names[c] for c in cols[: k.value]]
 
 
 def build_program(eng: Engine, relations: dict, rules: list, sinks: dict | None = None):

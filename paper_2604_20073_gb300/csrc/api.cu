@@ -973,73 +973,176 @@ int dl_relation_clear(dl_engine* e, dl_rel_id rel) {
     });
 }
 
+// Validate a rule given through the ABI and convert it (throws Error; changes nothing).
+Rule parse_rule(Engine& E, const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,
+                uint32_t nvars) {
+    if (!head || !body) throw Error(DL_ERR_ARG, "null head or body");
+    if (nbody == 0 || nbody > DL_MAX_BODY) throw Error(DL_ERR_ARG, "body size out of range");
+    Rule r;
+    auto read = [&](const dl_atom& a, RuleAtom& ra) {
+        Relation& R = rel_of(E, a.rel);
+        if (a.arity != R.user_arity) throw Error(DL_ERR_ARG, "arity mismatch for relation " + R.name);
+        if (!a.terms) throw Error(DL_ERR_ARG, "null terms");
+        ra.rel = a.rel;
+        ra.arity = a.arity;
+        for (uint32_t c = 0; c < a.arity; c++) {
+            if (a.terms[c].kind != DL_TERM_VAR && a.terms[c].kind != DL_TERM_CONST)
+                throw Error(DL_ERR_ARG, "bad term kind");
+            if (a.terms[c].kind == DL_TERM_VAR && a.terms[c].id >= 1024) throw Error(DL_ERR_ARG, "variable id >= 1024");
+            ra.terms[c] = a.terms[c];
+        }
+    };
+    std::set<uint32_t> bvars;
+    bool unsupported_const = false, unsupported_repeat = false;
+    for (uint32_t b = 0; b < nbody; b++) {
+        RuleAtom ra;
+        read(body[b], ra);
+        std::set<uint32_t> here;
+        for (uint32_t c = 0; c < ra.arity; c++) {
+            if (ra.terms[c].kind == DL_TERM_CONST) {
+                unsupported_const = true;
+                continue;
+            }
+            if (!here.insert(ra.terms[c].id).second) unsupported_repeat = true;
+            bvars.insert(ra.terms[c].id);
+        }
+        r.body.push_back(ra);
+    }
+    read(*head, r.head);
+    for (uint32_t c = 0; c < r.head.arity; c++)
+        if (r.head.terms[c].kind == DL_TERM_VAR && !bvars.count(r.head.terms[c].id))
+            throw Error(DL_ERR_ARG, "head variable not bound by the body");
+    if (bvars.size() + (E.instances ? 1 : 0) > DL_MAX_VARS) throw Error(DL_ERR_ARG, "too many variables");
+    if (!var_order || nvars != bvars.size()) throw Error(DL_ERR_ARG, "variable order must list every body variable once");
+    std::set<uint32_t> ord(var_order, var_order + nvars);
+    if (ord != bvars) throw Error(DL_ERR_ARG, "variable order is not a permutation of the body variables");
+    if (unsupported_const) throw Error(DL_ERR_UNSUPPORTED, "constants in body atoms are not supported on the GPU path");
+    if (unsupported_repeat)
+        throw Error(DL_ERR_UNSUPPORTED, "a variable repeated within one body atom is not supported on the GPU path");
+    r.order.assign(var_order, var_order + nvars);
+    if (E.instances) {
+        // batched form: the instance id is column 0 of every atom and the first join variable
+        const uint32_t inst_var = 0x7fffffffu;
+        auto shift = [&](RuleAtom& ra) {
+            for (uint32_t c = ra.arity; c > 0; c--) ra.terms[c] = ra.terms[c - 1];
+            ra.terms[0].kind = DL_TERM_VAR;
+            ra.terms[0].id = inst_var;
+            ra.arity++;
+        };
+        for (RuleAtom& b : r.body) shift(b);
+        shift(r.head);
+        r.order.insert(r.order.begin(), inst_var);
+    }
+    for (uint32_t c = 0; c < r.head.arity; c++)
+        if (r.head.terms[c].kind == DL_TERM_CONST && r.head.terms[c].id == 0xffffffffu)
+            throw Error(DL_ERR_UNSUPPORTED, "value 0xFFFFFFFF is reserved");
+    return r;
+}
+
+void add_rule(Engine& E, const Rule& r, dl_rule_id* out) {
+    for (uint32_t c = 0; c < r.head.arity; c++)
+        if (r.head.terms[c].kind == DL_TERM_CONST) E.V = std::max(E.V, r.head.terms[c].id + 1);
+    E.rules.push_back(r);
+    if (out) *out = (dl_rule_id)(E.rules.size() - 1);
+}
+
 int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,
                 uint32_t nvars, dl_rule_id* out) {
+    return guard(e, [&](Engine& E) { add_rule(E, parse_rule(E, head, body, nbody, var_order, nvars), out); });
+}
+
+// Helper-relation splitting (Section 5): the variables of the factored atoms that the rest of
+// the rule (other atoms or the head) also uses, in the rule's variable order.
+std::vector<uint32_t> split_columns(const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,
+                                    uint32_t nvars, uint64_t mask) {
+    if (!head || !body || !var_order) throw Error(DL_ERR_ARG, "null head, body or variable order");
+    if (nbody == 0 || nbody > DL_MAX_BODY) throw Error(DL_ERR_ARG, "body size out of range");
+    const uint64_t all = (1ull << nbody) - 1;
+    if (mask == 0 || (mask & ~all) || mask == all)
+        throw Error(DL_ERR_ARG, "the split must factor out a non-empty proper subset of the body atoms");
+    std::set<uint32_t> inside, outside;
+    auto vars = [](const dl_atom& a, std::set<uint32_t>& to) {
+        if (!a.terms) throw Error(DL_ERR_ARG, "null terms");
+        for (uint32_t c = 0; c < a.arity; c++)
+            if (a.terms[c].kind == DL_TERM_VAR) to.insert(a.terms[c].id);
+    };
+    for (uint32_t b = 0; b < nbody; b++) vars(body[b], ((mask >> b) & 1) ? inside : outside);
+    vars(*head, outside);
+    std::vector<uint32_t> cols;
+    for (uint32_t k = 0; k < nvars; k++)
+        if (inside.count(var_order[k]) && outside.count(var_order[k])) cols.push_back(var_order[k]);
+    if (cols.empty())
+        throw Error(DL_ERR_UNSUPPORTED, "the factored atoms share no variable with the rest of the rule");
+    return cols;
+}
+
+int dl_split_columns(const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,
+                     uint32_t nvars, uint64_t mask, uint32_t* cols, uint32_t cap, uint32_t* ncols) {
+    try {
+        const std::vector<uint32_t> c = split_columns(head, body, nbody, var_order, nvars, mask);
+        if (ncols) *ncols = (uint32_t)c.size();
+        if (cols) {
+            if (cap < c.size()) return DL_ERR_ARG;
+            std::copy(c.begin(), c.end(), cols);
+        }
+        return DL_OK;
+    } catch (const Error& ex) {
+        return ex.code;
+    } catch (...) {
+        return DL_ERR_ARG;
+    }
+}
+
+int dl_rule_add_split(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,
+                      uint32_t nvars, uint64_t mask, const char* helper_name, dl_rel_id* helper_rel,
+                      dl_rule_id* helper_rule, dl_rule_id* consumer_rule) {
     return guard(e, [&](Engine& E) {
-        if (!head || !body) throw Error(DL_ERR_ARG, "null head or body");
-        if (nbody == 0 || nbody > DL_MAX_BODY) throw Error(DL_ERR_ARG, "body size out of range");
-        Rule r;
-        auto read = [&](const dl_atom& a, RuleAtom& ra) {
-            Relation& R = rel_of(E, a.rel);
-            if (a.arity != R.user_arity) throw Error(DL_ERR_ARG, "arity mismatch for relation " + R.name);
-            if (!a.terms) throw Error(DL_ERR_ARG, "null terms");
-            ra.rel = a.rel;
-            ra.arity = a.arity;
-            for (uint32_t c = 0; c < a.arity; c++) {
-                if (a.terms[c].kind != DL_TERM_VAR && a.terms[c].kind != DL_TERM_CONST)
-                    throw Error(DL_ERR_ARG, "bad term kind");
-                if (a.terms[c].kind == DL_TERM_VAR && a.terms[c].id >= 1024) throw Error(DL_ERR_ARG, "variable id >= 1024");
-                ra.terms[c] = a.terms[c];
-            }
-        };
-        std::set<uint32_t> bvars;
-        bool unsupported_const = false, unsupported_repeat = false;
+        parse_rule(E, head, body, nbody, var_order, nvars);   // the unsplit rule must be valid
+        const std::vector<uint32_t> cols = split_columns(head, body, nbody, var_order, nvars, mask);
+        if (!helper_name || !*helper_name) throw Error(DL_ERR_ARG, "empty helper relation name");
+        for (auto& r : E.rels)
+            if (r.name == helper_name) throw Error(DL_ERR_ARG, std::string("duplicate relation name ") + helper_name);
+        if (cols.size() + (E.instances ? 1 : 0) > DL_MAX_ARITY)
+            throw Error(DL_ERR_UNSUPPORTED, "the helper relation would have more than DL_MAX_ARITY columns");
+        const dl_rel_id hid = (dl_rel_id)E.rels.size();
+        std::vector<dl_term> hterms;
+        for (uint32_t v : cols) hterms.push_back({DL_TERM_VAR, v});
+        const dl_atom hatom = {hid, (uint32_t)cols.size(), hterms.data()};
+        std::vector<dl_atom> hbody, cbody;
+        std::set<uint32_t> hvars, cvars(cols.begin(), cols.end());
         for (uint32_t b = 0; b < nbody; b++) {
-            RuleAtom ra;
-            read(body[b], ra);
-            std::set<uint32_t> here;
-            for (uint32_t c = 0; c < ra.arity; c++) {
-                if (ra.terms[c].kind == DL_TERM_CONST) {
-                    unsupported_const = true;
-                    continue;
-                }
-                if (!here.insert(ra.terms[c].id).second) unsupported_repeat = true;
-                bvars.insert(ra.terms[c].id);
-            }
-            r.body.push_back(ra);
+            const bool in = (mask >> b) & 1;
+            (in ? hbody : cbody).push_back(body[b]);
+            for (uint32_t c = 0; c < body[b].arity; c++)
+                if (body[b].terms[c].kind == DL_TERM_VAR) (in ? hvars : cvars).insert(body[b].terms[c].id);
         }
-        read(*head, r.head);
-        for (uint32_t c = 0; c < r.head.arity; c++)
-            if (r.head.terms[c].kind == DL_TERM_VAR && !bvars.count(r.head.terms[c].id))
-                throw Error(DL_ERR_ARG, "head variable not bound by the body");
-        if (bvars.size() + (E.instances ? 1 : 0) > DL_MAX_VARS) throw Error(DL_ERR_ARG, "too many variables");
-        if (!var_order || nvars != bvars.size()) throw Error(DL_ERR_ARG, "variable order must list every body variable once");
-        std::set<uint32_t> ord(var_order, var_order + nvars);
-        if (ord != bvars) throw Error(DL_ERR_ARG, "variable order is not a permutation of the body variables");
-        if (unsupported_const) throw Error(DL_ERR_UNSUPPORTED, "constants in body atoms are not supported on the GPU path");
-        if (unsupported_repeat)
-            throw Error(DL_ERR_UNSUPPORTED, "a variable repeated within one body atom is not supported on the GPU path");
-        r.order.assign(var_order, var_order + nvars);
-        if (E.instances) {
-            // batched form: the instance id is column 0 of every atom and the first join variable
-            const uint32_t inst_var = 0x7fffffffu;
-            auto shift = [&](RuleAtom& ra) {
-                for (uint32_t c = ra.arity; c > 0; c--) ra.terms[c] = ra.terms[c - 1];
-                ra.terms[0].kind = DL_TERM_VAR;
-                ra.terms[0].id = inst_var;
-                ra.arity++;
-            };
-            for (RuleAtom& b : r.body) shift(b);
-            shift(r.head);
-            r.order.insert(r.order.begin(), inst_var);
+        cbody.push_back(hatom);
+        std::vector<uint32_t> horder, corder;   // the rule's order restricted to each body
+        for (uint32_t k = 0; k < nvars; k++) {
+            if (hvars.count(var_order[k])) horder.push_back(var_order[k]);
+            if (cvars.count(var_order[k])) corder.push_back(var_order[k]);
         }
-        for (uint32_t c = 0; c < r.head.arity; c++)
-            if (r.head.terms[c].kind == DL_TERM_CONST) {
-                if (r.head.terms[c].id == 0xffffffffu) throw Error(DL_ERR_UNSUPPORTED, "value 0xFFFFFFFF is reserved");
-                E.V = std::max(E.V, r.head.terms[c].id + 1);
-            }
-        E.rules.push_back(r);
-        if (out) *out = (dl_rule_id)(E.rules.size() - 1);
+        // the helper relation exists while the two rules are checked; removed again on failure
+        Relation R;
+        R.name = helper_name;
+        R.arity = (uint32_t)cols.size() + (E.instances ? 1 : 0);
+        R.user_arity = (uint32_t)cols.size();
+        R.perms.push_back(identity_perm());
+        R.full.push_back(empty_index(R.arity, identity_perm()));
+        R.delta.push_back(empty_index(R.arity, identity_perm()));
+        R.root_needed.push_back(false);
+        E.rels.push_back(std::move(R));
+        Rule hr, cr;
+        try {
+            hr = parse_rule(E, &hatom, hbody.data(), (uint32_t)hbody.size(), horder.data(), (uint32_t)horder.size());
+            cr = parse_rule(E, head, cbody.data(), (uint32_t)cbody.size(), corder.data(), (uint32_t)corder.size());
+        } catch (...) {
+            E.rels.pop_back();
+            throw;
+        }
+        add_rule(E, hr, helper_rule);
+        add_rule(E, cr, consumer_rule);
+        if (helper_rel) *helper_rel = hid;
     });
 }
 

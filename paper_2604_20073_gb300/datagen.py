@@ -252,3 +252,50 @@ def hub_graph(hubs: int, n: int, m: int, seed: int) -> np.ndarray:
     r = random_graph(n - hubs, m, seed) + np.uint32(hubs)
     rows = np.concatenate([star, star[:, ::-1], hh, r, r[:, ::-1]])
     return unique_rows(rows)
+
+
+def call_graph_facts(scale: float, seed: int) -> dict:
+    """Facts shaped like the virtual-call resolution step of a Java points-to analysis (the
+    CallGraphEdge rule): methods, invocation sites, variables, heap objects and types, with
+    Zipf-skewed heaps, method names, descriptors and types so that a few types (the
+    java.lang.Object-like base classes) own most heap objects and answer most method lookups.
+
+    Sizes at scale 1: 2,000 methods (60% reachable), 20,000 invocations, 10,000 variables,
+    20,000 heaps, 500 types, 200 simple names x 20 descriptors.  Returns name -> rows:
+    Reachable(j), InstructionMethod(i, j), VirtualMethodInvoc(i, b, sn, dsc),
+    VarPointsTo(h, b), HeapAllocationType(h, t), MethodLookup(sn, dsc, t, m); every
+    relation deduplicated and sorted."""
+    M = max(2, int(round(2_000 * scale)))
+    I = max(2, int(round(20_000 * scale)))
+    B = max(2, int(round(10_000 * scale)))
+    H = max(2, int(round(20_000 * scale)))
+    T, NS, ND = 500, 200, 20
+    pos = 0
+
+    def take(cnt):
+        nonlocal pos
+        s = pos
+        pos += cnt
+        return s
+
+    reach = _uniform_ids(seed, take(int(0.6 * M)), int(0.6 * M), M).reshape(-1, 1)
+    im = np.stack([np.arange(I, dtype=np.uint32), _uniform_ids(seed, take(I), I, M)], axis=1)
+    vmi = np.stack([np.arange(I, dtype=np.uint32), _uniform_ids(seed, take(I), I, B),
+                    _zipf_ranks(seed, take(I), I, NS, 1.1), _zipf_ranks(seed, take(I), I, ND, 1.1)], axis=1)
+    n_vpt = 3 * B
+    vpt = np.stack([_zipf_ranks(seed, take(n_vpt), n_vpt, H, 1.1), _uniform_ids(seed, take(n_vpt), n_vpt, B)], axis=1)
+    hat = np.stack([np.arange(H, dtype=np.uint32), _zipf_ranks(seed, take(H), H, T, 1.3)], axis=1)
+    # each type answers 20 lookups, the 5 most common types 320 more (their methods are
+    # inherited everywhere); the resolved method is a hash of (sn, dsc, t)
+    per = np.full(T, 20, dtype=np.int64)
+    per[:5] += 300
+    t_col = np.repeat(np.arange(T, dtype=np.uint32), per)
+    n_ml = len(t_col)
+    sn = _zipf_ranks(seed, take(n_ml), n_ml, NS, 1.1)
+    dsc = _zipf_ranks(seed, take(n_ml), n_ml, ND, 1.1)
+    key = (sn.astype(np.uint64) << np.uint64(40)) | (dsc.astype(np.uint64) << np.uint64(20)) | t_col.astype(np.uint64)
+    m = (_mix(key ^ np.uint64(seed & 0xFFFFFFFF)) % np.uint64(M)).astype(np.uint32)
+    ml = np.stack([sn, dsc, t_col, m], axis=1)
+    return {"Reachable": unique_rows(reach), "InstructionMethod": unique_rows(im),
+            "VirtualMethodInvoc": unique_rows(vmi), "VarPointsTo": unique_rows(vpt),
+            "HeapAllocationType": unique_rows(hat), "MethodLookup": unique_rows(ml)}

@@ -46,3 +46,26 @@ SG = [
     (("SG", ["x", "y"]), [("Edge", ["a", "x"]), ("SG", ["a", "b"]), ("Edge", ["b", "y"])], ["a", "b", "x", "y"]),
 ]
 SG_RELS = {"Edge": 2, "SG": 2}
+
+# Virtual-call resolution of a Java points-to analysis (the paper's CallGraphEdge example,
+# Section 5): six atoms, eight variables; HeapAllocationType and MethodLookup (positions 4
+# and 5) are the atoms the paper factors into a helper relation.
+CGE = [
+    (("CallGraphEdge", ["i", "m"]),
+     [("Reachable", ["j"]), ("InstructionMethod", ["i", "j"]), ("VirtualMethodInvoc", ["i", "b", "sn", "dsc"]),
+      ("VarPointsTo", ["h", "b"]), ("HeapAllocationType", ["h", "t"]), ("MethodLookup", ["sn", "dsc", "t", "m"])],
+     ["j", "i", "b", "sn", "dsc", "h", "t", "m"]),
+]
+CGE_RELS = {"Reachable": 1, "InstructionMethod": 2, "VirtualMethodInvoc": 4, "VarPointsTo": 2,
+            "HeapAllocationType": 2, "MethodLookup": 4, "CallGraphEdge": 2}
+CGE_SPLIT = (4, 5)
+# the same split written out by hand: helper over the variables shared with the rest
+CGE_HELPER = [
+    (("HelpNT", ["sn", "dsc", "h", "m"]),
+     [("HeapAllocationType", ["h", "t"]), ("MethodLookup", ["sn", "dsc", "t", "m"])],
+     ["sn", "dsc", "h", "t", "m"]),
+    (("CallGraphEdge", ["i", "m"]),
+     [("Reachable", ["j"]), ("InstructionMethod", ["i", "j"]), ("VirtualMethodInvoc", ["i", "b", "sn", "dsc"]),
+      ("VarPointsTo", ["h", "b"]), ("HelpNT", ["sn", "dsc", "h", "m"])],
+     ["j", "i", "b", "sn", "dsc", "h", "m"]),
+]
