@@ -1,4 +1,4 @@
-"""CPU oracle for positive Datalog (test infrastructure only).
+"""CPU oracle for Datalog with stratified negation and comparisons (test infrastructure only).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 may import this package.  It shares no code with the GPU library; the product never
@@ -14,9 +14,11 @@ Program format (plain data, built by the caller):
 * ``relations``: ``{name: arity}``
 * ``facts``: ``{name: (rows, arity) uint32 array}``
 * ``rules``: list of ``(head, body)`` where ``head`` is an atom and ``body`` a list of
-  atoms; an atom is ``(relation_name, [term, ...])``; a term is a ``str`` (variable)
-  or an ``int`` (constant).  A rule may carry a third item, a variable order, which is
-  ignored: the oracle's result does not depend on one.
+  items; an atom is ``(relation_name, [term, ...])``; a term is a ``str`` (variable)
+  or an ``int`` (constant).  A body item is an atom, a negated atom ``("not", atom)``
+  or a comparison ``(op, term, term)`` with op one of ``<  <=  >  >=  !=`` (unsigned
+  32-bit order).  A rule may carry a third item, a variable order, which is ignored: the
+  oracle's result does not depend on one.
 """
 from __future__ import annotations
 
@@ -61,6 +63,10 @@ def _load():
             lib.orc_add_facts.argtypes = [ctypes.c_void_p, ctypes.c_int, u32p, ctypes.c_uint64]
             lib.orc_add_rule.argtypes = [ctypes.c_void_p, ctypes.c_int, u32p, u32p, ctypes.c_uint32,
                                          ctypes.POINTER(ctypes.c_int32), u32p, u32p]
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            lib.orc_add_rule_ex.argtypes = [ctypes.c_void_p, ctypes.c_int, u32p, u32p, ctypes.c_uint32, i32p, u32p,
+                                            u32p, ctypes.c_uint32, i32p, u32p, u32p, ctypes.c_uint32, u32p, u32p,
+                                            u32p]
             lib.orc_run.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_count.restype = ctypes.c_uint64
             lib.orc_count.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -125,19 +131,50 @@ def evaluate(relations: dict, facts: dict, rules: list, mode: str = "seminaive")
                         vals.append(int(t))
                 return kinds, vals
             var_ids: dict = {}
+            pos, neg, cmps = [], [], []
+            for item in body:
+                if len(item) == 3:
+                    cmps.append(item)
+                elif item[0] == "not":
+                    neg.append(item[1])
+                else:
+                    pos.append(item)
             bk, bv, brels = [], [], []
-            for rel, terms in body:
+            for rel, terms in pos:
                 k, v = enc(terms, rel)
                 bk += k
                 bv += v
                 brels.append(rid[rel])
+            nk, nv, nrels = [], [], []
+            for rel, terms in neg:
+                k, v = enc(terms, rel)
+                nk += k
+                nv += v
+                nrels.append(rid[rel])
+            ops, ck, cv = [], [], []
+            for op, a, b in cmps:
+                if op in (">", ">="):
+                    op, a, b = ("<" if op == ">" else "<="), b, a
+                ops.append({"<": 0, "<=": 1, "!=": 2}[op])
+                for t in (a, b):
+                    if isinstance(t, str):
+                        if t not in var_ids:
+                            raise OracleError(f"comparison variable {t} not bound by a positive atom")
+                        ck.append(0)
+                        cv.append(var_ids[t])
+                    else:
+                        ck.append(1)
+                        cv.append(int(t))
             hk, hv = enc(head[1], head[0])
-            arr = lambda x: np.asarray(x, dtype=np.uint32)  # noqa: E731
-            hk_a, hv_a, bk_a, bv_a = arr(hk), arr(hv), arr(bk), arr(bv)
-            br_a = np.asarray(brels, dtype=np.int32)
-            ok = lib.orc_add_rule(h, rid[head[0]], _u32(hk_a), _u32(hv_a), len(body),
-                                  br_a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                  _u32(bk_a), _u32(bv_a))
+            arr = lambda x: np.asarray(x if len(x) else [0], dtype=np.uint32)  # noqa: E731
+            arr_i = lambda x: np.asarray(x if len(x) else [0], dtype=np.int32)  # noqa: E731
+            hk_a, hv_a, bk_a, bv_a, nk_a, nv_a = arr(hk), arr(hv), arr(bk), arr(bv), arr(nk), arr(nv)
+            ops_a, ck_a, cv_a = arr(ops), arr(ck), arr(cv)
+            br_a, nr_a = arr_i(brels), arr_i(nrels)
+            i32 = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))  # noqa: E731
+            ok = lib.orc_add_rule_ex(h, rid[head[0]], _u32(hk_a), _u32(hv_a), len(pos), i32(br_a),
+                                     _u32(bk_a), _u32(bv_a), len(neg), i32(nr_a), _u32(nk_a), _u32(nv_a),
+                                     len(cmps), _u32(ops_a), _u32(ck_a), _u32(cv_a))
             if ok < 0:
                 raise OracleError(lib.orc_error(h).decode())
         if lib.orc_run(h, MODES[mode]) != 0:

@@ -1,5 +1,6 @@
 /*
- * Oracle: a plain, slow, obviously-correct CPU evaluator of positive Datalog.
+ * Oracle: a plain, slow, obviously-correct CPU evaluator of Datalog with stratified
+ * negation and comparison filters.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's
  * CPU-baseline leg may load this library.  It shares no code, header or helper with the
@@ -10,6 +11,16 @@
  * stratum (relation dependency graph -> strongly connected components, each SCC run
  * to its own fixpoint and then frozen).  Shared variables are equality constraints;
  * constants and a variable repeated inside one atom act as filters.
+ *
+ * Negation and comparisons (the extension the paper lists in Table 1 and leaves
+ * unspecified; the reading used here): a rule may carry negated atoms "not R(...)" and
+ * comparisons "a < b", "a <= b", "a != b" between variables or constants (unsigned 32-bit
+ * order).  Every variable of a negated atom or comparison must occur in a positive body
+ * atom (safety).  A binding of the positive atoms yields the head tuple iff every
+ * comparison holds and no negated atom's tuple is present.  A negated relation must be
+ * complete before the rule runs: the program is stratified with negated atoms as
+ * dependency edges, and a negated relation in the head's own component is an error (not
+ * stratifiable).  Negated relations are read in full in every round.
  *
  * Three evaluators:
  *  - ORC_SEMINAIVE: semi-naive evaluation (Section 2, the differential rule
@@ -25,7 +36,8 @@
  *    over the active domain is tried and kept if every body tuple is present.
  *  - ORC_NAIVE_GLOBAL: the same brute-force T_P iterated over all rules at once, with
  *    no stratification at all (the least model of a positive program does not depend
- *    on stratification).
+ *    on stratification).  Refused for programs with negation, whose meaning needs the
+ *    strata.
  *
  * Readings of points the paper leaves open (each stated again where used):
  *  - Rounds of a stratum: round 1 evaluates the non-recursive rules of the stratum;
@@ -43,9 +55,12 @@
 #define ORC_MAX_ARITY 8
 #define ORC_MAX_VARS 16
 #define ORC_MAX_BODY 16
+#define ORC_MAX_NEG 8
+#define ORC_MAX_CMP 16
 
 enum { ORC_SEMINAIVE = 0, ORC_NAIVE_STRATA = 1, ORC_NAIVE_GLOBAL = 2 };
 enum { T_VAR = 0, T_CONST = 1 };
+enum { CMP_LT = 0, CMP_LE = 1, CMP_NE = 2 };
 
 /* ------------------------------------------------------------------ tables */
 
@@ -145,10 +160,15 @@ static int table_insert(table* t, const uint32_t* v) {
 
 typedef struct { uint32_t kind, val; } term;
 typedef struct { int32_t rel; uint32_t arity; term t[ORC_MAX_ARITY]; } atom;
+typedef struct { uint32_t op; term a, b; } comparison;
 typedef struct {
     atom head;
     uint32_t nbody;
     atom body[ORC_MAX_BODY];
+    uint32_t nneg;
+    atom neg[ORC_MAX_NEG];          /* negated atoms */
+    uint32_t ncmp;
+    comparison cmp[ORC_MAX_CMP];
     uint32_t nvars;                 /* variables are renumbered 0..nvars-1 */
 } rule;
 
@@ -239,12 +259,16 @@ static int read_atom(program* p, atom* a, int32_t rel, const uint32_t* kinds, co
     return 0;
 }
 
-/* body_kinds / body_vals hold the terms of all body atoms back to back. */
-int orc_add_rule(void* h, int head_rel, const uint32_t* head_kinds, const uint32_t* head_vals,
-                 uint32_t nbody, const int32_t* body_rels, const uint32_t* body_kinds,
-                 const uint32_t* body_vals) {
+/* body_kinds / body_vals hold the terms of all body atoms back to back; the same for the
+ * negated atoms.  Comparison c is "term 2c  op[c]  term 2c+1" over cmp_kinds / cmp_vals. */
+int orc_add_rule_ex(void* h, int head_rel, const uint32_t* head_kinds, const uint32_t* head_vals,
+                    uint32_t nbody, const int32_t* body_rels, const uint32_t* body_kinds,
+                    const uint32_t* body_vals, uint32_t nneg, const int32_t* neg_rels,
+                    const uint32_t* neg_kinds, const uint32_t* neg_vals, uint32_t ncmp,
+                    const uint32_t* cmp_ops, const uint32_t* cmp_kinds, const uint32_t* cmp_vals) {
     program* p = (program*)h;
     if (nbody < 1 || nbody > ORC_MAX_BODY) return fail(p, "body size out of range");
+    if (nneg > ORC_MAX_NEG || ncmp > ORC_MAX_CMP) return fail(p, "too many negated atoms or comparisons");
     rule r;
     memset(&r, 0, sizeof(r));
     uint32_t var_map[1024];
@@ -256,9 +280,31 @@ int orc_add_rule(void* h, int head_rel, const uint32_t* head_kinds, const uint32
         off += p->arity[body_rels[b]];
     }
     uint32_t nbody_vars = nv;
+    off = 0;
+    for (uint32_t b = 0; b < nneg; b++) {
+        if (neg_rels[b] < 0 || (uint32_t)neg_rels[b] >= p->nrel) return fail(p, "bad relation in rule");
+        if (read_atom(p, &r.neg[b], neg_rels[b], neg_kinds + off, neg_vals + off, var_map, &nv)) return -1;
+        off += p->arity[neg_rels[b]];
+    }
+    for (uint32_t c = 0; c < ncmp; c++) {
+        if (cmp_ops[c] > CMP_NE) return fail(p, "bad comparison");
+        r.cmp[c].op = cmp_ops[c];
+        term* t[2] = {&r.cmp[c].a, &r.cmp[c].b};
+        for (int s = 0; s < 2; s++) {
+            const uint32_t k = cmp_kinds[2 * c + s], v = cmp_vals[2 * c + s];
+            if (k == T_CONST) { t[s]->kind = T_CONST; t[s]->val = v; continue; }
+            if (k != T_VAR || v >= 1024) return fail(p, "bad term in comparison");
+            if (var_map[v] == UINT32_MAX) return fail(p, "comparison variable not bound by a positive atom");
+            t[s]->kind = T_VAR;
+            t[s]->val = var_map[v];
+        }
+    }
+    if (nv != nbody_vars) return fail(p, "negated atom variable not bound by a positive atom");
     if (read_atom(p, &r.head, head_rel, head_kinds, head_vals, var_map, &nv)) return -1;
     if (nv != nbody_vars) return fail(p, "head variable not bound by the body");
     r.nbody = nbody;
+    r.nneg = nneg;
+    r.ncmp = ncmp;
     r.nvars = nv;
     if (p->nrule == p->caprule) {
         p->caprule = p->caprule ? p->caprule * 2 : 8;
@@ -266,6 +312,33 @@ int orc_add_rule(void* h, int head_rel, const uint32_t* head_kinds, const uint32
     }
     p->rules[p->nrule++] = r;
     return (int)(p->nrule - 1);
+}
+
+int orc_add_rule(void* h, int head_rel, const uint32_t* head_kinds, const uint32_t* head_vals,
+                 uint32_t nbody, const int32_t* body_rels, const uint32_t* body_kinds,
+                 const uint32_t* body_vals) {
+    return orc_add_rule_ex(h, head_rel, head_kinds, head_vals, nbody, body_rels, body_kinds, body_vals, 0, NULL,
+                           NULL, NULL, 0, NULL, NULL, NULL);
+}
+
+/* The rule's filters for one binding of its variables: every comparison holds and no
+ * negated atom's tuple is in its (complete, lower-stratum) relation. */
+static int filters_hold(const program* p, const rule* r, const uint32_t* vals) {
+    for (uint32_t c = 0; c < r->ncmp; c++) {
+        const comparison* q = &r->cmp[c];
+        const uint32_t a = q->a.kind == T_CONST ? q->a.val : vals[q->a.val];
+        const uint32_t b = q->b.kind == T_CONST ? q->b.val : vals[q->b.val];
+        if (q->op == CMP_LT && !(a < b)) return 0;
+        if (q->op == CMP_LE && !(a <= b)) return 0;
+        if (q->op == CMP_NE && !(a != b)) return 0;
+    }
+    for (uint32_t n = 0; n < r->nneg; n++) {
+        const atom* a = &r->neg[n];
+        uint32_t tup[ORC_MAX_ARITY];
+        for (uint32_t c = 0; c < a->arity; c++) tup[c] = a->t[c].kind == T_CONST ? a->t[c].val : vals[a->t[c].val];
+        if (table_contains(&p->full[a->rel], tup)) return 0;
+    }
+    return 1;
 }
 
 /* ------------------------------------------------------------ stratification */
@@ -297,7 +370,7 @@ static void tarjan_visit(tarjan_state* s, uint32_t v) {
     }
 }
 
-static void stratify(program* p) {
+static int stratify(program* p) {
     free_strata(p);
     uint32_t n = p->nrel;
     tarjan_state s;
@@ -305,15 +378,18 @@ static void stratify(program* p) {
     s.n = n;
     s.adj_off = (uint32_t*)xcalloc(n + 1, sizeof(uint32_t));
     uint32_t ne = 0;
-    for (uint32_t i = 0; i < p->nrule; i++) ne += p->rules[i].nbody;
+    for (uint32_t i = 0; i < p->nrule; i++) ne += p->rules[i].nbody + p->rules[i].nneg;
     s.adj = (uint32_t*)xcalloc(ne, sizeof(uint32_t));
-    for (uint32_t i = 0; i < p->nrule; i++)
+    for (uint32_t i = 0; i < p->nrule; i++) {
         for (uint32_t b = 0; b < p->rules[i].nbody; b++) s.adj_off[p->rules[i].body[b].rel + 1]++;
+        for (uint32_t b = 0; b < p->rules[i].nneg; b++) s.adj_off[p->rules[i].neg[b].rel + 1]++;
+    }
     for (uint32_t v = 0; v < n; v++) s.adj_off[v + 1] += s.adj_off[v];
     uint32_t* fill = (uint32_t*)xcalloc(n, sizeof(uint32_t));
     for (uint32_t i = 0; i < p->nrule; i++)
-        for (uint32_t b = 0; b < p->rules[i].nbody; b++) {
-            uint32_t u = (uint32_t)p->rules[i].body[b].rel;
+        for (uint32_t b = 0; b < p->rules[i].nbody + p->rules[i].nneg; b++) {
+            const atom* a = b < p->rules[i].nbody ? &p->rules[i].body[b] : &p->rules[i].neg[b - p->rules[i].nbody];
+            uint32_t u = (uint32_t)a->rel;
             s.adj[s.adj_off[u] + fill[u]++] = (uint32_t)p->rules[i].head.rel;
         }
     s.index = (uint32_t*)xmalloc(n * sizeof(uint32_t));
@@ -364,8 +440,13 @@ static void stratify(program* p) {
     p->strata_off[ns] = nr;
     p->nstrata = ns;
     p->rounds = (uint32_t*)xcalloc(ns ? ns : 1, sizeof(uint32_t));
+    int stratifiable = 1;
+    for (uint32_t i = 0; i < p->nrule; i++)
+        for (uint32_t b = 0; b < p->rules[i].nneg; b++)
+            if (s.comp[p->rules[i].neg[b].rel] == s.comp[p->rules[i].head.rel]) stratifiable = 0;
     free(s.adj_off); free(s.adj); free(fill); free(s.index); free(s.low); free(s.stack);
     free(s.comp); free(s.on); free(minrel); free(indeg); free(has_rule); free(done); free(order);
+    return stratifiable ? 0 : fail(p, "negation inside a recursive component: the program is not stratifiable");
 }
 
 /* ------------------------------------------------- hash-indexed nested loops */
@@ -413,6 +494,7 @@ typedef struct {
 static void emit_head(join_ctx* j) {
     uint32_t tup[ORC_MAX_ARITY];
     const atom* h = &j->r->head;
+    if (!filters_hold(j->p, j->r, j->vals)) return;
     for (uint32_t c = 0; c < h->arity; c++) tup[c] = h->t[c].kind == T_CONST ? h->t[c].val : j->vals[h->t[c].val];
     table_insert(j->out, tup);
 }
@@ -564,10 +646,14 @@ static domain active_domain(const program* p) {
         for (uint64_t i = 0; i < p->full[r].n * p->arity[r]; i++) table_insert(&seen, &p->full[r].rows[i]);
     for (uint32_t i = 0; i < p->nrule; i++) {
         const rule* r = &p->rules[i];
-        for (uint32_t b = 0; b <= r->nbody; b++) {
-            const atom* a = b < r->nbody ? &r->body[b] : &r->head;
+        for (uint32_t b = 0; b <= r->nbody + r->nneg; b++) {
+            const atom* a = b < r->nbody ? &r->body[b] : b < r->nbody + r->nneg ? &r->neg[b - r->nbody] : &r->head;
             for (uint32_t c = 0; c < a->arity; c++)
                 if (a->t[c].kind == T_CONST) table_insert(&seen, &a->t[c].val);
+        }
+        for (uint32_t c = 0; c < r->ncmp; c++) {
+            if (r->cmp[c].a.kind == T_CONST) table_insert(&seen, &r->cmp[c].a.val);
+            if (r->cmp[c].b.kind == T_CONST) table_insert(&seen, &r->cmp[c].b.val);
         }
     }
     for (uint64_t i = 0; i < seen.n; i++) {
@@ -593,6 +679,7 @@ static void brute_rule(const program* p, const rule* r, const domain* d, table* 
             for (uint32_t c = 0; c < a->arity; c++) tup[c] = a->t[c].kind == T_CONST ? a->t[c].val : vals[a->t[c].val];
             ok = table_contains(&p->full[a->rel], tup);
         }
+        if (ok) ok = filters_hold(p, r, vals);
         if (ok) {
             uint32_t tup[ORC_MAX_ARITY];
             for (uint32_t c = 0; c < r->head.arity; c++)
@@ -629,7 +716,10 @@ static uint32_t naive_iterate(program* p, const domain* d, int32_t stratum) {
 
 int orc_run(void* h, int mode) {
     program* p = (program*)h;
-    stratify(p);
+    if (stratify(p)) return -1;
+    if (mode == ORC_NAIVE_GLOBAL)
+        for (uint32_t i = 0; i < p->nrule; i++)
+            if (p->rules[i].nneg) return fail(p, "global naive iteration is undefined for negation");
     if (mode == ORC_SEMINAIVE) {
         for (uint32_t s = 0; s < p->nstrata; s++) seminaive_stratum(p, s);
         return 0;

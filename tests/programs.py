@@ -69,3 +69,20 @@ CGE_HELPER = [
       ("VarPointsTo", ["h", "b"]), ("HelpNT", ["sn", "dsc", "h", "m"])],
      ["j", "i", "b", "sn", "dsc", "h", "m"]),
 ]
+
+# Comparisons and stratified negation (the extension Table 1 lists; semantics fixed by the
+# oracle's reading).  Oriented cliques count each clique once.
+TRI_LT = [(("TriLt", ["x", "y", "z"]),
+           [("E", ["x", "y"]), ("E", ["y", "z"]), ("E", ["x", "z"]), ("<", "x", "y"), ("<", "y", "z")],
+           ["x", "y", "z"])]
+Q4_LT = [(("Q4Lt", ["w", "x", "y", "z"]),
+          [("E", ["w", "x"]), ("E", ["w", "y"]), ("E", ["w", "z"]), ("E", ["x", "y"]), ("E", ["x", "z"]),
+           ("E", ["y", "z"]), ("<", "w", "x"), ("<", "x", "y"), ("<", "y", "z")],
+          ["w", "x", "y", "z"])]
+# vertices, their reachability, and the pairs that do not reach each other
+UNREACH = TC + [
+    (("Node", ["x"]), [("E", ["x", "y"])], ["x", "y"]),
+    (("Node", ["y"]), [("E", ["x", "y"])], ["x", "y"]),
+    (("Unreach", ["x", "y"]), [("Node", ["x"]), ("Node", ["y"]), ("not", ("Reach", ["x", "y"]))], ["x", "y"]),
+]
+UNREACH_RELS = {"E": 2, "Reach": 2, "Node": 1, "Unreach": 2}
