@@ -46,6 +46,8 @@ extern "C" {
 #define DL_MAX_ARITY 8        /* columns per relation */
 #define DL_MAX_VARS 12        /* distinct variables per rule */
 #define DL_MAX_BODY 12        /* atoms per rule body; at most 8 of them may mention one variable */
+#define DL_MAX_NEG 4          /* negated atoms per rule (dl_rule_add_ex) */
+#define DL_MAX_CMP 8          /* comparisons per rule (dl_rule_add_ex) */
 #define DL_MAX_STRATA 64      /* strata reported in dl_stats (more may exist) */
 
 /* dl_config.flags */
@@ -180,6 +182,34 @@ typedef struct dl_atom {
  * > DL_MAX_BODY, more than DL_MAX_VARS variables), DL_ERR_UNSUPPORTED, DL_ERR_STATE. */
 int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody,
                 const uint32_t* var_order, uint32_t nvars, dl_rule_id* out);
+
+/* Comparison filter "a op b" over unsigned 32-bit values; a and b are variables of the rule
+ * or constants (dl_term). */
+#define DL_CMP_LT 0u          /* a <  b */
+#define DL_CMP_LE 1u          /* a <= b */
+#define DL_CMP_NE 2u          /* a != b */
+typedef struct dl_cmp {
+    uint32_t op;              /* DL_CMP_* */
+    dl_term a, b;
+} dl_cmp;
+
+/* dl_rule_add with negated atoms and comparisons (stratified negation and comparison
+ * filters, the extension listed in Table 1; the paper leaves their semantics open, the
+ * reading here): a binding of the positive atoms body[0..nbody) yields the head tuple iff
+ * every comparison cmps[0..ncmp) holds and no negated atom neg[0..nneg) has its tuple in
+ * its relation.  Every variable of a negated atom or comparison must occur in a positive
+ * atom (safety); var_order lists the positive atoms' variables.  A negated relation is
+ * read complete: dl_fixpoint stratifies with negated atoms as dependency edges and
+ * evaluates a negated relation's stratum first; a negated relation in the head's own
+ * recursive component makes dl_fixpoint fail with DL_ERR_UNSUPPORTED (not stratifiable).
+ * A filter is applied in the join at the level of its last variable in var_order.
+ * GPU path limits: negated atoms take distinct variables only (constants or a repeated
+ * variable: DL_ERR_UNSUPPORTED).
+ * Errors: as dl_rule_add; DL_ERR_ARG (nneg > DL_MAX_NEG, ncmp > DL_MAX_CMP, bad op, an
+ * unbound filter variable, a negated count sink). */
+int dl_rule_add_ex(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody,
+                   const dl_atom* neg, uint32_t nneg, const dl_cmp* cmps, uint32_t ncmp,
+                   const uint32_t* var_order, uint32_t nvars, dl_rule_id* out);
 
 /* Helper-relation splitting (Section 5, the CallGraphEdge example): add a rule in two parts.
  * The body atoms selected by `mask` (bit b = body[b]) are factored out into a helper rule

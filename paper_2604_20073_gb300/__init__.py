@@ -34,6 +34,7 @@ DL_FLAG_PROFILE = 0x4
 KERNEL_KINDS = ["join_hist", "join_count", "join_write", "scan", "sort", "delta", "merge", "other"]
 DL_SINK_STORE, DL_SINK_COUNT = 0, 1
 DL_TERM_VAR, DL_TERM_CONST = 0, 1
+DL_CMP_LT, DL_CMP_LE, DL_CMP_NE = 0, 1, 2
 DL_MAX_STRATA = 64
 
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -52,6 +53,10 @@ class dl_config(ctypes.Structure):
 
 class dl_term(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("id", ctypes.c_uint32)]
+
+
+class dl_cmp(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint32), ("a", dl_term), ("b", dl_term)]
 
 
 class dl_atom(ctypes.Structure):
@@ -120,6 +125,9 @@ _SIGS = {
     "dl_relation_clear": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "dl_rule_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_atom), ctypes.POINTER(dl_atom),
                                    ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p]),
+    "dl_rule_add_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_atom), ctypes.POINTER(dl_atom),
+                                      ctypes.c_uint32, ctypes.POINTER(dl_atom), ctypes.c_uint32,
+                                      ctypes.POINTER(dl_cmp), ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p]),
     "dl_rule_add_split": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_atom), ctypes.POINTER(dl_atom),
                                          ctypes.c_uint32, _u32p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_char_p,
                                          _u32p, _u32p, _u32p]),
@@ -318,16 +326,38 @@ class Engine:
         return a
 
     def rule(self, head, body, order):
+        """Add a rule.  body items: atoms (rel, [terms]), negated atoms ("not", atom) and
+        comparisons (op, term, term) with op in < <= > >= != (dl_rule_add_ex)."""
         var_ids: dict = {}
         keep: list = []
-        batoms = (dl_atom * len(body))()
-        for i, b in enumerate(body):
+        pos = [b for b in body if len(b) == 2 and b[0] != "not"]
+        neg = [b[1] for b in body if len(b) == 2 and b[0] == "not"]
+        cmps = [b for b in body if len(b) == 3]
+        batoms = (dl_atom * len(pos))()
+        for i, b in enumerate(pos):
             batoms[i] = self._atom(b, var_ids, keep)
+        natoms = (dl_atom * max(1, len(neg)))()
+        for i, b in enumerate(neg):
+            natoms[i] = self._atom(b, var_ids, keep)
+        carr = (dl_cmp * max(1, len(cmps)))()
+        for i, (op, a, b) in enumerate(cmps):
+            if op in (">", ">="):
+                op, a, b = ("<" if op == ">" else "<="), b, a
+            carr[i].op = {"<": DL_CMP_LT, "<=": DL_CMP_LE, "!=": DL_CMP_NE}[op]
+            for t, dst in ((a, carr[i].a), (b, carr[i].b)):
+                if isinstance(t, str):
+                    dst.kind, dst.id = DL_TERM_VAR, var_ids.get(t, 1023)
+                else:
+                    dst.kind, dst.id = DL_TERM_CONST, int(t)
         h = self._atom(head, var_ids, keep)
         ordr = (ctypes.c_uint32 * len(order))(*[var_ids.get(v, 1023) for v in order])
         rid = ctypes.c_uint32()
-        self._check(self.lib.dl_rule_add(self.h, ctypes.byref(h), batoms, len(body), ordr, len(order),
-                                         ctypes.byref(rid)))
+        if neg or cmps:
+            self._check(self.lib.dl_rule_add_ex(self.h, ctypes.byref(h), batoms, len(pos), natoms, len(neg), carr,
+                                                len(cmps), ordr, len(order), ctypes.byref(rid)))
+        else:
+            self._check(self.lib.dl_rule_add(self.h, ctypes.byref(h), batoms, len(pos), ordr, len(order),
+                                             ctypes.byref(rid)))
         return rid.value
 
     def rule_split(self, head, body, order, factored, helper: str):

@@ -12,6 +12,7 @@
 namespace dl {
 
 Perm atom_perm(const Rule& R, uint32_t a);
+Perm neg_perm(const Rule& R, uint32_t n);
 bool head_is_order(const Rule& R);
 
 // ------------------------------------------------------------------ memory
@@ -361,6 +362,10 @@ std::vector<Stratum> stratify(const Engine& E) {
             g[a.rel].push_back(r.head.rel);
             gr[r.head.rel].push_back(a.rel);
         }
+        for (const RuleAtom& a : r.neg) {     // a negated relation is computed first
+            g[a.rel].push_back(r.head.rel);
+            gr[r.head.rel].push_back(a.rel);
+        }
     }
     std::vector<uint32_t> finish;
     std::vector<bool> seen(n, false);
@@ -399,6 +404,12 @@ std::vector<Stratum> stratify(const Engine& E) {
         }
         nc++;
     }
+    for (const Rule& r : E.rules)
+        for (const RuleAtom& a : r.neg)
+            if (comp[a.rel] == comp[r.head.rel])
+                throw Error(DL_ERR_UNSUPPORTED, "relation '" + E.rels[a.rel].name +
+                                                    "' is negated inside its own recursive component: the program is "
+                                                    "not stratifiable");
     std::vector<std::set<int>> succ(nc);
     std::vector<int> indeg(nc, 0), minrel(nc, INT32_MAX);
     for (uint32_t v = 0; v < n; v++) minrel[comp[v]] = std::min(minrel[comp[v]], (int)v);
@@ -570,6 +581,11 @@ void run_variant(Engine& E, const Variant& v, std::map<uint32_t, PendingOut>& ou
         uint32_t slot = perm_slot(B, atom_perm(r, (uint32_t)a));
         src[a] = (int)a == v.delta_atom ? &B.delta[slot] : &B.full[slot];
     }
+    std::vector<const Index*> nsrc(r.neg.size());   // negated relations: lower strata, read in full
+    for (size_t a = 0; a < r.neg.size(); a++) {
+        Relation& B = E.rels[r.neg[a].rel];
+        nsrc[a] = &B.full[perm_slot(B, neg_perm(r, (uint32_t)a))];
+    }
     Relation& H = E.rels[r.head.rel];
     PendingOut& po = outs[r.head.rel];
     JoinOutput jo;
@@ -578,7 +594,7 @@ void run_variant(Engine& E, const Variant& v, std::map<uint32_t, PendingOut>& ou
             Index rp = reduce_part(E, H, buf, t);
             if (rp.n) jo.rparts.push_back(rp);
         };
-    run_join(E, r, src, H, jo);
+    run_join(E, r, src, nsrc, H, jo);
     if (!jo.parts.empty() || !jo.rparts.empty()) {
         po.producers++;
         po.out.sorted_unique = (po.producers == 1) && jo.sorted_unique && jo.rparts.empty();
@@ -625,12 +641,17 @@ void fixpoint(Engine& E, dl_stats* st) {
     validate_program(E);
     for (Relation& R : E.rels) flush_pending(E, R);
     // plan: index permutations each atom reads; roots for every index a join probes
-    for (const Rule& r : E.rules)
+    for (const Rule& r : E.rules) {
         for (uint32_t a = 0; a < r.body.size(); a++) {
             Relation& B = E.rels[r.body[a].rel];
             uint32_t slot = perm_slot(B, atom_perm(r, a));
             B.root_needed[slot] = true;
         }
+        for (uint32_t a = 0; a < r.neg.size(); a++) {
+            Relation& B = E.rels[r.neg[a].rel];
+            B.root_needed[perm_slot(B, neg_perm(r, a))] = true;
+        }
+    }
     for (Relation& R : E.rels) {
         if (R.sink == DL_SINK_COUNT) {
             R.sink_count = 0;
@@ -975,9 +996,12 @@ int dl_relation_clear(dl_engine* e, dl_rel_id rel) {
 
 // Validate a rule given through the ABI and convert it (throws Error; changes nothing).
 Rule parse_rule(Engine& E, const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,
-                uint32_t nvars) {
+                uint32_t nvars, const dl_atom* neg = nullptr, uint32_t nneg = 0, const dl_cmp* cmps = nullptr,
+                uint32_t ncmp = 0) {
     if (!head || !body) throw Error(DL_ERR_ARG, "null head or body");
     if (nbody == 0 || nbody > DL_MAX_BODY) throw Error(DL_ERR_ARG, "body size out of range");
+    if (nneg > DL_MAX_NEG || ncmp > DL_MAX_CMP) throw Error(DL_ERR_ARG, "too many negated atoms or comparisons");
+    if ((nneg && !neg) || (ncmp && !cmps)) throw Error(DL_ERR_ARG, "null negated atoms or comparisons");
     Rule r;
     auto read = [&](const dl_atom& a, RuleAtom& ra) {
         Relation& R = rel_of(E, a.rel);
@@ -1012,6 +1036,36 @@ Rule parse_rule(Engine& E, const dl_atom* head, const dl_atom* body, uint32_t nb
     for (uint32_t c = 0; c < r.head.arity; c++)
         if (r.head.terms[c].kind == DL_TERM_VAR && !bvars.count(r.head.terms[c].id))
             throw Error(DL_ERR_ARG, "head variable not bound by the body");
+    bool neg_unsupported = false;
+    for (uint32_t n = 0; n < nneg; n++) {
+        RuleAtom ra;
+        read(neg[n], ra);
+        if (E.rels[ra.rel].sink == DL_SINK_COUNT) throw Error(DL_ERR_ARG, "a count sink cannot be negated");
+        std::set<uint32_t> here;
+        for (uint32_t c = 0; c < ra.arity; c++) {
+            if (ra.terms[c].kind == DL_TERM_CONST) {
+                neg_unsupported = true;
+                continue;
+            }
+            if (!bvars.count(ra.terms[c].id)) throw Error(DL_ERR_ARG, "negated atom variable not bound by a positive atom");
+            if (!here.insert(ra.terms[c].id).second) neg_unsupported = true;
+        }
+        r.neg.push_back(ra);
+    }
+    for (uint32_t k = 0; k < ncmp; k++) {
+        const dl_cmp& q = cmps[k];
+        if (q.op > DL_CMP_NE) throw Error(DL_ERR_ARG, "bad comparison operator");
+        for (const dl_term* t : {&q.a, &q.b}) {
+            if (t->kind != DL_TERM_VAR && t->kind != DL_TERM_CONST) throw Error(DL_ERR_ARG, "bad term kind");
+            if (t->kind == DL_TERM_VAR && !bvars.count(t->id))
+                throw Error(DL_ERR_ARG, "comparison variable not bound by a positive atom");
+        }
+        RuleCmp rc;
+        rc.op = q.op;
+        rc.a = q.a;
+        rc.b = q.b;
+        r.cmps.push_back(rc);
+    }
     if (bvars.size() + (E.instances ? 1 : 0) > DL_MAX_VARS) throw Error(DL_ERR_ARG, "too many variables");
     if (!var_order || nvars != bvars.size()) throw Error(DL_ERR_ARG, "variable order must list every body variable once");
     std::set<uint32_t> ord(var_order, var_order + nvars);
@@ -1019,6 +1073,8 @@ Rule parse_rule(Engine& E, const dl_atom* head, const dl_atom* body, uint32_t nb
     if (unsupported_const) throw Error(DL_ERR_UNSUPPORTED, "constants in body atoms are not supported on the GPU path");
     if (unsupported_repeat)
         throw Error(DL_ERR_UNSUPPORTED, "a variable repeated within one body atom is not supported on the GPU path");
+    if (neg_unsupported)
+        throw Error(DL_ERR_UNSUPPORTED, "negated atoms take distinct variables only on the GPU path");
     r.order.assign(var_order, var_order + nvars);
     if (E.instances) {
         // batched form: the instance id is column 0 of every atom and the first join variable
@@ -1030,6 +1086,7 @@ Rule parse_rule(Engine& E, const dl_atom* head, const dl_atom* body, uint32_t nb
             ra.arity++;
         };
         for (RuleAtom& b : r.body) shift(b);
+        for (RuleAtom& b : r.neg) shift(b);
         shift(r.head);
         r.order.insert(r.order.begin(), inst_var);
     }
@@ -1074,6 +1131,14 @@ std::vector<uint32_t> split_columns(const dl_atom* head, const dl_atom* body, ui
     if (cols.empty())
         throw Error(DL_ERR_UNSUPPORTED, "the factored atoms share no variable with the rest of the rule");
     return cols;
+}
+
+int dl_rule_add_ex(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody, const dl_atom* neg,
+                   uint32_t nneg, const dl_cmp* cmps, uint32_t ncmp, const uint32_t* var_order, uint32_t nvars,
+                   dl_rule_id* out) {
+    return guard(e, [&](Engine& E) {
+        add_rule(E, parse_rule(E, head, body, nbody, var_order, nvars, neg, nneg, cmps, ncmp), out);
+    });
 }
 
 int dl_split_columns(const dl_atom* head, const dl_atom* body, uint32_t nbody, const uint32_t* var_order,

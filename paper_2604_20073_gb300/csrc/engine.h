@@ -40,9 +40,16 @@ struct RuleAtom {
     dl_term terms[kMaxArity];
 };
 
+struct RuleCmp {
+    uint32_t op = 0;                  // DL_CMP_*
+    dl_term a{}, b{};
+};
+
 struct Rule {
     RuleAtom head;
     std::vector<RuleAtom> body;
+    std::vector<RuleAtom> neg;        // negated atoms (relations of lower strata)
+    std::vector<RuleCmp> cmps;        // comparison filters
     std::vector<uint32_t> order;      // user variable ids in join order
 };
 
@@ -159,6 +166,8 @@ struct JoinOutput {
     // chunk and appends it as a reduced part.
     std::function<void(DevPtr, TableView)> chunk_sink;
 };
-void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Relation& head, JoinOutput& out);
+// src: the index each positive body atom reads; nsrc: each negated atom's (complete) index.
+void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, const std::vector<const Index*>& nsrc,
+              Relation& head, JoinOutput& out);
 
 }  // namespace dl

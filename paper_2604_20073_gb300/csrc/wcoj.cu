@@ -41,6 +41,10 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint8_t kVirtual = 0xff;   // source = the entry's sibling run in the frontier
 
 enum { MODE_FRONTIER = 0, MODE_HEAD = 1, MODE_COUNT = 2 };
+// A comparison applied at a level: relation of the level's value v to the other operand.
+enum { F_LT = 0, F_LE = 1, F_GT = 2, F_GE = 3, F_NE = 4 };
+constexpr int kMaxNeg = DL_MAX_NEG;
+constexpr int kMaxCmp = DL_MAX_CMP;
 
 struct LevelParams {
     AtomView atom[kMaxAtoms];
@@ -81,7 +85,36 @@ struct LevelParams {
     uint32_t head_const[kMaxArity];
     uint32_t* ocol[kMaxArity];
     unsigned long long* digest;           // MODE_COUNT: [count, sum, xor]
+    // filters whose last variable is this level's (comparisons, negated atoms)
+    uint32_t ncmp, nneg;
+    uint8_t cmp_op[kMaxCmp];              // F_*: v op w
+    int8_t cmp_pos[kMaxCmp];              // order position of w, -1 = the constant cmp_const
+    uint32_t cmp_const[kMaxCmp];
+    AtomView neg[kMaxNeg];                // a negated atom's index, columns in order-position order
+    int8_t neg_pos[kMaxNeg][kMaxArity];   // order position of each of its columns (the last: level)
 };
+
+// The level's filters for candidate v of entry e: every comparison holds and no negated
+// atom holds the bound tuple.
+__device__ __noinline__ bool filters_pass(const LevelParams& P, uint64_t e, uint32_t v) {
+    for (uint32_t f = 0; f < P.ncmp; f++) {
+        const uint32_t w = P.cmp_pos[f] < 0 ? P.cmp_const[f] : __ldg(P.fval[P.cmp_pos[f]] + e);
+        const uint8_t op = P.cmp_op[f];
+        const bool ok = op == F_LT ? v < w : op == F_LE ? v <= w : op == F_GT ? v > w : op == F_GE ? v >= w : v != w;
+        if (!ok) return false;
+    }
+    for (uint32_t n = 0; n < P.nneg; n++) {
+        const AtomView& A = P.neg[n];
+        uint32_t lo = 0, hi = A.n;
+        bool in = A.n > 0;
+        for (uint32_t c = 0; c < A.arity && in; c++) {
+            const int pos = P.neg_pos[n][c];
+            in = narrow(A, (int)c, pos == (int)P.level ? v : __ldg(P.fval[pos] + e), lo, hi);
+        }
+        if (in) return false;
+    }
+    return true;
+}
 
 // Row range of source s for frontier entry e, and the column its candidates live in.
 __device__ __forceinline__ const uint32_t* src_range(const LevelParams& P, int s, uint64_t e, uint32_t& lo,
@@ -139,7 +172,9 @@ struct Unit {
     uint32_t lo[kMaxSrc + 1], hi[kMaxSrc + 1];
 };
 
-// Decode unit u of the flat space into (entry, local) and evaluate it.
+// Decode unit u of the flat space into (entry, local) and evaluate it (F: the level has
+// filters).
+template <bool F>
 __device__ __forceinline__ bool eval_unit(const LevelParams& P, uint64_t u, uint64_t e0, uint64_t e1, Unit& U) {
     uint64_t e;
     if (P.naive) e = e0;
@@ -190,6 +225,7 @@ __device__ __forceinline__ bool eval_unit(const LevelParams& P, uint64_t u, uint
         U.lo[s] = lo;
         U.hi[s] = hi;
     }
+    if (F && !filters_pass(P, e, v)) return false;
     return true;
 }
 
@@ -244,6 +280,7 @@ __device__ __forceinline__ void tile_entries(const LevelParams& P, uint64_t tlo,
     e1 = s_e1;
 }
 
+template <bool F>
 __global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count(const __grid_constant__ LevelParams P) {
     uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
@@ -251,7 +288,7 @@ __global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count(const __grid_con
     unsigned long long cnt = 0, hs = 0, hx = 0;
     Unit U;
     for (uint64_t u = tlo + threadIdx.x; u < thi; u += blockDim.x) {
-        if (!eval_unit(P, u, e0, e1, U)) continue;
+        if (!eval_unit<F>(P, u, e0, e1, U)) continue;
         cnt++;
         if (P.mode == MODE_COUNT) {
             uint64_t h = kTupleHashSeed;
@@ -304,6 +341,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_
     return pre + x - v;
 }
 
+template <bool F>
 __global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_write(const __grid_constant__ LevelParams P) {
     uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
@@ -312,7 +350,7 @@ __global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_write(const __grid_con
     Unit U;
     for (uint64_t base = tlo; base < thi; base += blockDim.x) {
         const uint64_t u = base + threadIdx.x;
-        const uint32_t f = (u < thi && eval_unit(P, u, e0, e1, U)) ? 1u : 0u;
+        const uint32_t f = (u < thi && eval_unit<F>(P, u, e0, e1, U)) ? 1u : 0u;
         uint32_t total;
         const uint32_t pos = block_exclusive_scan_u32(f, total);
         if (f) {
@@ -505,7 +543,7 @@ __device__ __forceinline__ uint32_t head_value(const LevelParams& P, int c, uint
     return pos < 0 ? P.head_const[c] : __ldg(P.fval[pos] + e);
 }
 
-template <int NS>
+template <int NS, bool F>
 __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm(const __grid_constant__ LevelParams P) {
     const int lane = threadIdx.x & 31;
     // the warp's range lives in shared memory between entries (registers are the limit here)
@@ -538,6 +576,7 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
                 const uint32_t rr = b + lane;
                 uint32_t v, nlo[EntryState<NS>::NP], nhi[EntryState<NS>::NP], dnlo, dnhi;
                 if (rr >= stop || !entry_eval(P, S, rr + S.eoff, v, nlo, nhi, dnlo, dnhi)) continue;
+                if (F && !filters_pass(P, e, v)) continue;
                 cnt++;
                 if (P.mode == MODE_COUNT) {
                     uint64_t h = tuple_hash_step(hpre, v, P.head_lvl);
@@ -569,7 +608,7 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
     }
 }
 
-template <int NS>
+template <int NS, bool F>
 __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 6 : 4) k_wcoj_write_wm(const __grid_constant__ LevelParams P) {
     const int lane = threadIdx.x & 31;
     uint64_t wlo, whi;
@@ -586,7 +625,8 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 6 : 4) k_wcoj_write_wm
         for (uint32_t b = r; b < stop; b += 32) {
             const uint32_t rr = b + lane;
             uint32_t v = 0, nlo[EntryState<NS>::NP], nhi[EntryState<NS>::NP], dnlo = 0, dnhi = 0;
-            const bool f = rr < stop && entry_eval(P, S, rr + S.eoff, v, nlo, nhi, dnlo, dnhi);
+            const bool f = rr < stop && entry_eval(P, S, rr + S.eoff, v, nlo, nhi, dnlo, dnhi) &&
+                           (!F || filters_pass(P, e, v));
             const unsigned ball = __ballot_sync(kFull, f);
             if (f) {
                 const uint64_t w = o + __popc(ball & lt);
@@ -631,13 +671,19 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 6 : 4) k_wcoj_write_wm
     }
 }
 
-#define DL_NS_DISPATCH(KERNEL, NSRC, GRID, STREAM, PARAMS)                                              \
+#define DL_NS_DISPATCH_F(KERNEL, NSRC, F, GRID, STREAM, PARAMS)                                     \
     do {                                                                                            \
-        if ((NSRC) <= 1) KERNEL<1><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);                  \
-        else if ((NSRC) <= 2) KERNEL<2><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);             \
-        else if ((NSRC) <= 3) KERNEL<3><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);             \
-        else if ((NSRC) <= 4) KERNEL<4><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);             \
-        else KERNEL<kMaxSrc + 1><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);                   \
+        if ((NSRC) <= 1) KERNEL<1, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);               \
+        else if ((NSRC) <= 2) KERNEL<2, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);          \
+        else if ((NSRC) <= 3) KERNEL<3, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);          \
+        else if ((NSRC) <= 4) KERNEL<4, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);          \
+        else KERNEL<kMaxSrc + 1, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);                \
+    } while (0)
+// by source count and by whether the level has filters
+#define DL_NS_DISPATCH(KERNEL, NSRC, FILT, GRID, STREAM, PARAMS)                                    \
+    do {                                                                                            \
+        if (FILT) DL_NS_DISPATCH_F(KERNEL, NSRC, true, GRID, STREAM, PARAMS);                       \
+        else DL_NS_DISPATCH_F(KERNEL, NSRC, false, GRID, STREAM, PARAMS);                           \
     } while (0)
 
 // Sibling runs of a frontier: seg[k] = 1 if entry k starts a new parent's run.
@@ -674,7 +720,10 @@ struct Plan {
     std::vector<uint32_t> defer_mask;       // per level: atoms whose depth-0 check moves to their next level
 };
 
-Plan make_plan(const Rule& R, const std::vector<const Index*>& idx) {
+// filter_levels: bit l set when level l applies a comparison or a negated atom; the level
+// after it then cannot reuse its siblings (they passed filters on the previous variable
+// that need not hold for the next one).
+Plan make_plan(const Rule& R, const std::vector<const Index*>& idx, uint64_t filter_levels) {
     Plan p;
     p.m = (uint32_t)R.order.size();
     p.natoms = (uint32_t)R.body.size();
@@ -705,6 +754,7 @@ Plan make_plan(const Rule& R, const std::vector<const Index*>& idx) {
     // the match possible.  Reuse is only taken when it replaces an intersection of >= 2
     // sources.
     for (uint32_t l = 1; l < p.m; l++) {
+        if ((filter_levels >> (l - 1)) & 1u) continue;
         uint32_t defer = 0;
         std::vector<Src> applied;
         for (const Src& b : p.src[l - 1]) {
@@ -781,6 +831,70 @@ Perm atom_perm(const Rule& R, uint32_t a) {
     return p;
 }
 
+// Index permutation a negated atom needs: the same rule as for positive atoms.
+Perm neg_perm(const Rule& R, uint32_t n) {
+    const RuleAtom& A = R.neg[n];
+    std::vector<std::pair<int, int>> pc;
+    for (uint32_t c = 0; c < A.arity; c++)
+        pc.push_back({(int)(std::find(R.order.begin(), R.order.end(), A.terms[c].id) - R.order.begin()), (int)c});
+    std::sort(pc.begin(), pc.end());
+    Perm p = identity_perm();
+    for (uint32_t k = 0; k < A.arity; k++) p[k] = (uint8_t)pc[k].second;
+    return p;
+}
+
+// Filters of a rule placed at the level of their last variable.
+struct LevelFilters {
+    std::vector<uint8_t> op;
+    std::vector<int8_t> pos;
+    std::vector<uint32_t> cst;
+    std::vector<int> neg;                     // negated atom ids
+};
+
+// Returns false when a comparison can never hold (the rule derives nothing).
+bool place_filters(const Rule& R, const std::vector<const Index*>& nsrc, std::vector<LevelFilters>& lf,
+                   uint64_t& levels) {
+    auto pos_of = [&](uint32_t id) {
+        return (int)(std::find(R.order.begin(), R.order.end(), id) - R.order.begin());
+    };
+    lf.assign(R.order.size(), LevelFilters());
+    levels = 0;
+    for (const RuleCmp& q : R.cmps) {
+        const bool av = q.a.kind == DL_TERM_VAR, bv = q.b.kind == DL_TERM_VAR;
+        if (!av && !bv) {
+            const uint32_t a = q.a.id, b = q.b.id;
+            if (!(q.op == DL_CMP_LT ? a < b : q.op == DL_CMP_LE ? a <= b : a != b)) return false;
+            continue;
+        }
+        if (av && bv && q.a.id == q.b.id) {
+            if (q.op != DL_CMP_LE) return false;   // x < x and x != x never hold
+            continue;
+        }
+        const int pa = av ? pos_of(q.a.id) : -1, pb = bv ? pos_of(q.b.id) : -1;
+        // v is the operand bound last; op is rewritten as "v op' w"
+        const bool v_is_a = pa > pb;
+        uint8_t op;
+        if (q.op == DL_CMP_NE) op = F_NE;
+        else if (q.op == DL_CMP_LT) op = v_is_a ? F_LT : F_GT;
+        else op = v_is_a ? F_LE : F_GE;
+        const int lvl = v_is_a ? pa : pb;
+        const dl_term& w = v_is_a ? q.b : q.a;
+        LevelFilters& L = lf[lvl];
+        L.op.push_back(op);
+        L.pos.push_back(w.kind == DL_TERM_VAR ? (int8_t)pos_of(w.id) : (int8_t)-1);
+        L.cst.push_back(w.kind == DL_TERM_VAR ? 0u : w.id);
+        levels |= 1ull << lvl;
+    }
+    for (uint32_t n = 0; n < R.neg.size(); n++) {
+        if (nsrc[n]->n == 0) continue;        // nothing to exclude
+        int lvl = 0;
+        for (uint32_t c = 0; c < R.neg[n].arity; c++) lvl = std::max(lvl, pos_of(R.neg[n].terms[c].id));
+        lf[lvl].neg.push_back((int)n);
+        levels |= 1ull << lvl;
+    }
+    return true;
+}
+
 // True when a rule's head lists exactly the variable order: the join then emits rows that are
 // already sorted in the head's canonical order and distinct.
 bool head_is_order(const Rule& R) {
@@ -790,8 +904,12 @@ bool head_is_order(const Rule& R) {
     return true;
 }
 
-void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Relation& head, JoinOutput& out) {
-    const Plan plan = make_plan(R, src);
+void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, const std::vector<const Index*>& nsrc,
+              Relation& head, JoinOutput& out) {
+    std::vector<LevelFilters> lf;
+    uint64_t filter_levels = 0;
+    if (!place_filters(R, nsrc, lf, filter_levels)) return;   // a comparison that never holds
+    const Plan plan = make_plan(R, src, filter_levels);
     const bool count_sink = head.sink == DL_SINK_COUNT;
     out.sorted_unique = head_is_order(R);
 
@@ -843,6 +961,24 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
         }
         P.seg = f_seg;
         P.segstart = f_segstart;
+        {   // this level's filters
+            const LevelFilters& L = lf[lvl];
+            P.ncmp = (uint32_t)L.op.size();
+            P.nneg = (uint32_t)L.neg.size();
+            for (uint32_t f = 0; f < P.ncmp; f++) {
+                P.cmp_op[f] = L.op[f];
+                P.cmp_pos[f] = L.pos[f];
+                P.cmp_const[f] = L.cst[f];
+            }
+            for (uint32_t k = 0; k < P.nneg; k++) {
+                const int n = L.neg[k];
+                const Perm np = neg_perm(R, (uint32_t)n);
+                P.neg[k] = atom_of(*nsrc[n]);
+                for (uint32_t c = 0; c < R.neg[n].arity; c++)
+                    P.neg_pos[k][c] = (int8_t)(std::find(R.order.begin(), R.order.end(), R.neg[n].terms[np[c]].id) -
+                                               R.order.begin());
+            }
+        }
         // sources of this level (atoms covered by candidate reuse become one sibling source)
         P.nsrc = 0;
         for (const Src& s : plan.src[lvl]) {
@@ -904,12 +1040,16 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, Re
         auto bc = E.array<uint64_t>(ncounts + 1);
         P.block_count = (unsigned long long*)bc.p;
         auto launch_count = [&]() {
-            if (wm) DL_NS_DISPATCH(k_wcoj_count_wm, P.nsrc, (unsigned)ntiles, E.stream, P);
-            else k_wcoj_count<<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+            const bool filt = P.ncmp || P.nneg;
+            if (wm) DL_NS_DISPATCH(k_wcoj_count_wm, P.nsrc, filt, (unsigned)ntiles, E.stream, P);
+            else if (filt) k_wcoj_count<true><<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
+            else k_wcoj_count<false><<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
         };
         auto launch_write = [&](uint64_t grid) {
-            if (wm) DL_NS_DISPATCH(k_wcoj_write_wm, P.nsrc, (unsigned)grid, E.stream, P);
-            else k_wcoj_write<<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
+            const bool filt = P.ncmp || P.nneg;
+            if (wm) DL_NS_DISPATCH(k_wcoj_write_wm, P.nsrc, filt, (unsigned)grid, E.stream, P);
+            else if (filt) k_wcoj_write<true><<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
+            else k_wcoj_write<false><<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
         };
 
         if (last && count_sink) {
