@@ -53,10 +53,10 @@ def parse():
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="cyclic", choices=["cyclic", "batched", "served", "split"],
+    ap.add_argument("--workload", default="cyclic", choices=["cyclic", "batched", "served", "split", "oriented"],
                     help="cyclic: the Tri + Q4 fixpoint line (default); batched: 4096 TC+Tri instances; "
                          "served: Poisson request mix through the serving loop; split: helper-relation "
-                         "splitting ablation on CallGraphEdge")
+                         "splitting ablation on CallGraphEdge; oriented: Tri + Q4 with comparison filters")
     ap.add_argument("--cge-scale", type=float, default=20.0)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--instances", type=int, default=4096)
@@ -514,12 +514,61 @@ def run_split_workload(args):
                       "clocks": clk}))
 
 
+def run_oriented_workload(args):
+    """Comparison filters: Tri and Q4 with x < y < z (w < x < y < z) on the bench graph, i.e.
+    each triangle and 4-clique once, against the unfiltered rules whose counts are 6x / 24x."""
+    import numpy as np
+    import torch
+
+    import paper_2604_20073_gb300 as pkg
+    e, cfg = workload(args.scale)
+    dev = torch.device("cuda", 0)
+    tri_lt = [(("TriLt", ["x", "y", "z"]), [("E", ["x", "y"]), ("E", ["y", "z"]), ("E", ["x", "z"]),
+                                           ("<", "x", "y"), ("<", "y", "z")], ["x", "y", "z"])]
+    q4_lt = [(("Q4Lt", ["w", "x", "y", "z"]), [("E", ["w", "x"]), ("E", ["w", "y"]), ("E", ["w", "z"]),
+                                              ("E", ["x", "y"]), ("E", ["x", "z"]), ("E", ["y", "z"]),
+                                              ("<", "w", "x"), ("<", "x", "y"), ("<", "y", "z")],
+              ["w", "x", "y", "z"])]
+    eng = pkg.Engine(flags=pkg.DL_FLAG_PROFILE)
+    pkg.build_program(eng, {"E": 2, "TriLt": 3, "Q4Lt": 4}, tri_lt + q4_lt, {"Q4Lt": pkg.DL_SINK_COUNT})
+    eng.load("E", torch.from_numpy(np.ascontiguousarray(e.T)).to(dev))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    clocks = Clocks(0)
+    times, st = [], None
+    for k in range(args.warmup + args.steps):
+        eng.clear("TriLt")
+        eng.clear("Q4Lt")
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = eng.fixpoint()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    tri, q4 = int(st["join_rows"]), int(st["count_rows"])
+    print(json.dumps({"metric": "fixpoint s and WCOJ tuples/s (oriented Tri + 4-clique: comparison filters)",
+                      "value": (tri + q4) / (ms / 1e3), "unit": "tuples/s", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "u32",
+                      "data": "synthetic", "config": dict(cfg, workload=cfg["workload"].replace("Tri + Q4", "TriLt + Q4Lt")),
+                      "results": {"TriLt_rows": tri, "Q4Lt_rows": q4, "Tri_x6": 6 * tri, "Q4_x24": 24 * q4},
+                      "kernels_ms_per_step": {k: round(v["ms"], 2) for k, v in st["kernels"].items() if v["launches"]},
+                      "gpu_launches": int(st["kernel_launches"]), "clocks": clk}))
+    eng.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "split":
         return run_split_workload(args)
+    if args.workload == "oriented":
+        return run_oriented_workload(args)
     if args.workload == "batched":
         return run_batched_workload(args)
     if args.workload == "served":
