@@ -685,7 +685,11 @@ def main():
                "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": cfg,
                "results": {"Tri_rows": int(stats[-1]["join_rows"]), "Q4_rows": int(stats[-1]["count_rows"]),
                            "rounds": stats[-1]["rounds"], "peak_bytes": int(stats[-1]["peak_bytes"]),
-                           "hub_keys": int(stats[-1]["hub_keys"])},
+                           "hub_keys": int(stats[-1]["hub_keys"]),
+                           "fixpoint_s": ms / 1e3,
+                           # the join phases only (histogram, count, scan, materialise)
+                           "wcoj_tuples_per_s_join_phases": (tuples / (stats[-1]["ms_join"] / 1e3)
+                                                             if stats[-1]["ms_join"] > 0 else None)},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(out))
     eng.close()
