@@ -219,17 +219,21 @@ void build_hubs(Engine& E, Index& ix) {
         keys[i] = heavy[i].second;
         slot[heavy[i].second] = (int32_t)i;
     }
-    ix.hub = E.make(sizeof(int32_t) * V);
-    ix.bits = E.make(sizeof(uint32_t) * (uint64_t)bmwords * keys.size());
+    // the index takes the bitmaps only once they are complete (an allocation that fails
+    // leaves it without any)
+    DevPtr hub = E.make(sizeof(int32_t) * V);
+    DevPtr bits = E.make(sizeof(uint32_t) * (uint64_t)bmwords * keys.size());
     auto dkeys = E.array<uint32_t>(keys.size());
-    DL_CUDA(cudaMemcpyAsync(ix.hub->ptr, slot.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, E.stream));
+    DL_CUDA(cudaMemcpyAsync(hub->ptr, slot.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, E.stream));
     DL_CUDA(cudaMemcpyAsync(dkeys.p, keys.data(), sizeof(uint32_t) * keys.size(), cudaMemcpyHostToDevice, E.stream));
     build_hub_bits(E, (const uint32_t*)ix.root->ptr, ix.col(1), dkeys.p, (uint32_t)keys.size(),
-                   (uint32_t*)ix.bits->ptr, bmwords);
+                   (uint32_t*)bits->ptr, bmwords);
+    E.sync();   // the host vectors above must outlive the copies
+    ix.hub = hub;
+    ix.bits = bits;
     ix.bmwords = bmwords;
     ix.hubmin = heavy.back().first;
     E.hub_keys += keys.size();
-    E.sync();   // the host vectors above must outlive the copies
 }
 
 // Δ = unique(sorted new rows) \ full, written into a fresh index (canonical order).
