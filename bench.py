@@ -327,7 +327,8 @@ def served_pool(seed=1004):
     """Pre-generated inputs the requests draw from (generating a fresh multi-million-edge graph
     per request would dominate the run).  Sizes log-uniform per family, capped so that every
     result fits in memory: TC+Tri 1k-50k edges (|Reach| grows like nodes^2), 4-clique 1k-4M
-    edges, points-to scale 1/8192-1/1024 (larger scales saturate)."""
+    edges, points-to scale 1/8192-1/1024 (its derived relations grow to about half of their
+    full domains, so larger scales would dominate the mix)."""
     import numpy as np
 
     from paper_2604_20073_gb300 import datagen as dg
