@@ -81,6 +81,20 @@ def workload(scale):
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (the slowest rank's time bounds the job)."""
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, ms: float) -> float:
+    """Units per second of the whole job: every rank processes its own replica of the
+    workload (weak scaling), all of them within the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -629,11 +643,9 @@ def main():
     clk = clocks.stop()
     ms = statistics.mean(times)
     if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
     tuples = stats[-1]["join_rows"] + stats[-1]["count_rows"]
-    value = world * tuples / (ms / 1e3)
+    value = whole_job_rate(world, tuples, ms)
 
     # dominant kernel over the timed region (events on the engine's stream)
     agg = {k: {"launches": 0, "ms": 0.0, "alg_bytes": 0} for k in pkg.KERNEL_KINDS}
