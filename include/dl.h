@@ -254,7 +254,14 @@ int dl_split_columns(const dl_atom* head, const dl_atom* body, uint32_t nbody, c
 typedef struct dl_kernel_stat {
     uint64_t launches;        /* launches of this kind during the call */
     double ms;                /* summed device time (CUDA events on the engine's stream) */
-    uint64_t alg_bytes;       /* algorithmic bytes the launches had to move */
+    uint64_t alg_bytes;       /* algorithmic bytes the launches had to move: for a join
+                               * count or write pass 4*T + (entry bytes + 9)*F, T being the
+                               * candidates examined (each element of the smaller candidate
+                               * range, read once) and F the frontier entries, plus
+                               * 4*columns*rows written; for a merge 8*arity*(N + |delta|);
+                               * for a radix pass 4*n (histogram) or (4 + 8*arity)*n
+                               * (scatter); for dedup / anti-join 4*arity*n read (twice for
+                               * dedup) plus 4*arity*kept rows written */
 } dl_kernel_stat;
 
 typedef struct dl_stats {
@@ -453,8 +460,10 @@ int dl_server_get_stats(dl_server* s, dl_server_stats* out);
  * dcols_out[0..arity), each of which must hold nrows values; *nrows_out (host) receives the
  * number of distinct rows.  The result equals what dl_load_facts_device followed by
  * dl_fetch_device returns for an empty relation of that arity.  Inputs are not modified.
- * Work is issued on `stream` (a cudaStream_t; NULL = the default stream) and the call
- * synchronises that stream before returning.
+ * Work is issued on `stream` (a cudaStream_t; NULL = the default stream).  The call reads
+ * the number of distinct rows back to the host, so it waits for `stream` to finish before it
+ * returns.  A launch error still pending on the calling thread from earlier work is cleared
+ * at entry, so that DL_ERR_CUDA reports only this call's own failures.
  *
  * Memory: no allocation at all.  Scratch is one fixed static device array of about 8.1 MiB
  * (two DL_NOALLOC_MAX_ARITY x DL_NOALLOC_MAX_ROWS uint32 buffers plus counters), which every

@@ -211,6 +211,9 @@ extern "C" int dl_sort_unique_noalloc(const uint32_t* const* dcols_in, uint32_t 
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = (uint32_t)nrows;
     const uint32_t ntiles = (n + kTile - 1) / kTile;
+    // A launch error left pending on this thread by earlier, unrelated work would otherwise
+    // be reported below as this call's: take it off first.
+    (void)cudaGetLastError();
     Cols a, b, out;
     for (uint32_t c = 0; c < kMaxArity; c++) {
         a.c[c] = scratch + kOffA + (size_t)c * kMaxRows;

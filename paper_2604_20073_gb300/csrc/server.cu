@@ -40,6 +40,7 @@ struct Ticket {
     std::vector<RuleCopy> rules;
     std::vector<FactCopy> facts;
     uint64_t share = 0;
+    bool admitted = false;            // its share was added to the server's reservation
     int state = DL_REQ_QUEUED;
     int status = DL_OK;
     dl_engine* eng = nullptr;
@@ -133,6 +134,7 @@ void worker_loop(dl_server* s, size_t slot) {
             t = s->queue.front();
             s->queue.pop_front();
             s->reserved += t->share;
+            t->admitted = true;
             s->peak_reserved = std::max(s->peak_reserved, s->reserved);
             s->admitted++;
             s->running++;
@@ -305,7 +307,7 @@ int dl_server_release(dl_server* s, uint64_t ticket) {
     }
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        s->reserved -= t->share;
+        if (t->admitted) s->reserved -= t->share;   // a request drained at stop was never admitted
     }
     s->cv.notify_all();
     return DL_OK;

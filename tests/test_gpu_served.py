@@ -58,8 +58,10 @@ def test_mixed_requests_match_alone_and_oracle():
         left = set(range(len(reqs)))
         deadline = time.time() + 600
         order = []
+        max_running = 0
         while left:
             assert time.time() < deadline, srv.stats()
+            max_running = max(max_running, srv.stats()["running"])
             ready = [i for i in sorted(left) if srv.poll(tickets[i])[0] == pkg.DL_REQ_DONE]
             if not ready:
                 time.sleep(0.005)
@@ -84,6 +86,11 @@ def test_mixed_requests_match_alone_and_oracle():
         st = srv.stats()
         assert st["completed"] == len(reqs) and st["failed"] == 0
         assert st["peak_reserved_bytes"] <= 3 << 30
+        # continuous batching, not a queue alone: several requests held memory at once and
+        # several were evaluated at the same time on their slots' streams
+        assert st["peak_reserved_bytes"] >= 2 * (512 << 20)
+        assert max_running >= 2
+        assert st["reserved_bytes"] == 0
 
 
 def test_over_share_request_fails_alone():

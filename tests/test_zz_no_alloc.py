@@ -1,5 +1,6 @@
 """The allocation-free sort + dedup entry point (dl_sort_unique_noalloc) gives the same rows
-as the engine's own path (dl_load_facts_device + dl_fetch_device), on two calls in a row.
+as the engine's own path (dl_load_facts_device + dl_fetch_device) and as a host numpy
+sort + unique of the same rows, on two calls in a row.
 
 It exists for callers that may not allocate device memory while they run (a plugin whose
 host application's allocator owns the device budget, or a latency-bound loop that bans
@@ -38,6 +39,12 @@ def _engine_sort_unique(rows_dev, arity):
         return n, [c[:n].cpu().numpy().view(np.uint32) for c in cols]
 
 
+def _host_sort_unique(host):
+    """Sorted distinct rows computed on the host (numpy), independent of every GPU kernel."""
+    rows = np.unique(host.T, axis=0)          # lexicographic over columns 0..arity-1, unsigned
+    return [np.ascontiguousarray(rows[:, c]) for c in range(host.shape[0])]
+
+
 def test_noalloc_sort_unique_matches_engine_twice():
     import torch
     lib = pkg.load_library()
@@ -52,10 +59,12 @@ def test_noalloc_sort_unique_matches_engine_twice():
         rc, m = _noalloc(lib, cols_dev, out_dev, stream)
         assert rc == pkg.DL_OK
         n_ref, ref = _engine_sort_unique(rows_dev, arity)
-        assert m == n_ref
+        host_ref = _host_sort_unique(host)
+        assert m == n_ref == len(host_ref[0])
         for c in range(arity):
             got = out_dev[c][:m].cpu().numpy().view(np.uint32)
             assert np.array_equal(got, ref[c])
+            assert np.array_equal(got, host_ref[c])
         # the input columns are left untouched
         for c in range(arity):
             assert np.array_equal(cols_dev[c].cpu().numpy().view(np.uint32), host[c])
