@@ -74,6 +74,10 @@ def _load():
             lib.orc_num_strata.restype = ctypes.c_uint32
             lib.orc_num_strata.argtypes = [ctypes.c_void_p]
             lib.orc_stratum.argtypes = [ctypes.c_void_p, ctypes.c_uint32, u32p, u32p, u32p]
+            lib.orc_set_count_sink.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.orc_sink_digest.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+            lib.orc_join_seconds.restype = ctypes.c_double
+            lib.orc_join_seconds.argtypes = [ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -89,9 +93,11 @@ class OracleError(RuntimeError):
 class Result:
     """Per-relation sorted distinct rows and the strata with their round counts."""
 
-    def __init__(self, relations: dict, strata: list):
+    def __init__(self, relations: dict, strata: list, digests: dict | None = None, join_seconds: float = 0.0):
         self.relations = relations          # name -> (rows, arity) uint32, sorted, distinct
         self.strata = strata                # [(sorted relation names, rounds), ...] in evaluation order
+        self.digests = digests or {}        # count sinks: name -> (count, sum, xor), as tuple_digest
+        self.join_seconds = join_seconds    # time in the nested loops (hash index builds excluded)
 
     def rounds_of(self, name: str) -> int:
         for rels, r in self.strata:
@@ -100,8 +106,11 @@ class Result:
         raise KeyError(name)
 
 
-def evaluate(relations: dict, facts: dict, rules: list, mode: str = "seminaive") -> Result:
-    """Run a program to its least fixpoint and return every relation."""
+def evaluate(relations: dict, facts: dict, rules: list, mode: str = "seminaive",
+             sinks: tuple | list | set = ()) -> Result:
+    """Run a program to its least fixpoint and return every relation.  Relations named in
+    `sinks` are count sinks: they keep no rows (an empty array is returned for them) and
+    their count and digest, as tuple_digest defines it, go to Result.digests."""
     lib = _load()
     h = lib.orc_create()
     try:
@@ -112,6 +121,9 @@ def evaluate(relations: dict, facts: dict, rules: list, mode: str = "seminaive")
             if r < 0:
                 raise OracleError(lib.orc_error(h).decode())
             rid[name] = r
+        for name in sinks:
+            if lib.orc_set_count_sink(h, rid[name]) != 0:
+                raise OracleError(lib.orc_error(h).decode())
         for name, rows in facts.items():
             rows = np.ascontiguousarray(rows, dtype=np.uint32).reshape(-1, relations[name])
             if lib.orc_add_facts(h, rid[name], _u32(rows), rows.shape[0]) != 0:
@@ -193,26 +205,54 @@ def evaluate(relations: dict, facts: dict, rules: list, mode: str = "seminaive")
             rels = np.empty(len(names), dtype=np.uint32)
             lib.orc_stratum(h, s, ctypes.byref(rounds), _u32(rels), ctypes.byref(nrels))
             strata.append((sorted(names[i] for i in rels[: nrels.value]), rounds.value))
-        return Result(out, strata)
+        digests = {}
+        for name in sinks:
+            d = (ctypes.c_uint64 * 3)()
+            if lib.orc_sink_digest(h, rid[name], d) != 0:
+                raise OracleError(lib.orc_error(h).decode())
+            digests[name] = (int(d[0]), int(d[1]), int(d[2]))
+        return Result(out, strata, digests, float(lib.orc_join_seconds(h)))
     finally:
         lib.orc_destroy(h)
 
 
+_M64 = (1 << 64) - 1
+
+
+def splitmix64_mix(z: int) -> int:
+    """The splitmix64 output finaliser (Steele, Lea and Flood, 2014), on Python integers."""
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def row_hash(row) -> int:
+    """64-bit hash of one row: h = 0x243F6A8885A308D3; for column j with value v,
+    h = mix(h ^ (v + 0x9E3779B97F4A7C15 * (j + 1)))."""
+    h = 0x243F6A8885A308D3
+    for j, v in enumerate(row):
+        h = splitmix64_mix((h ^ ((int(v) + 0x9E3779B97F4A7C15 * (j + 1)) & _M64)) & _M64)
+    return h
+
+
 def tuple_digest(rows: np.ndarray) -> tuple:
-    """Order-independent digest of a set of rows: (count, sum mod 2^64, xor) of a 64-bit
-    hash of each row.  Row hash: h = 0x243F6A8885A308D3; for column j with value v,
-    h = mix(h ^ (v + 0x9E3779B97F4A7C15 * (j + 1))), mix being the splitmix64 finaliser.
-    Written here from that definition with Python integers, row by row."""
-    M = (1 << 64) - 1
+    """Order-independent digest of a set of rows: (count, sum mod 2^64, xor) of row_hash
+    over the rows.  Written here from that definition with Python integers, row by row."""
     s = 0
     x = 0
-    for row in np.asarray(rows, dtype=np.uint64).tolist():
-        h = 0x243F6A8885A308D3
-        for j, v in enumerate(row):
-            z = (h ^ ((v + 0x9E3779B97F4A7C15 * (j + 1)) & M)) & M
-            z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
-            z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
-            h = z ^ (z >> 31)
-        s = (s + h) & M
+    rows = np.asarray(rows, dtype=np.uint64)
+    for row in rows.tolist():
+        h = row_hash(row)
+        s = (s + h) & _M64
         x ^= h
     return (len(rows), s, x)
+
+
+def combine_digests(parts) -> tuple:
+    """Digest of the union of disjoint row sets from their digests."""
+    c = s = x = 0
+    for pc, ps, px in parts:
+        c += pc
+        s = (s + ps) & _M64
+        x ^= px
+    return (c, s, x)

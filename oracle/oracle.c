@@ -39,6 +39,19 @@
  *    on stratification).  Refused for programs with negation, whose meaning needs the
  *    strata.
  *
+ * Comparisons are checked in the nested loops as soon as all their variables are bound
+ * (and once more on the complete binding): a conjunction holds whatever order its terms are
+ * checked in, so this prunes work without changing which bindings pass.
+ *
+ * Count sinks (outputs too large to store, e.g. the 4-clique relation of a large graph): a
+ * relation marked with orc_set_count_sink keeps no tuples; every derived tuple instead adds
+ * to the relation's count and to its order-independent digest (sum mod 2^64 and xor of a
+ * 64-bit row hash; the row hash is h = 0x243F6A8885A308D3 and, for column j with value v,
+ * h = mix(h ^ (v + 0x9E3779B97F4A7C15 * (j + 1))), mix being the splitmix64 finaliser).
+ * This equals the digest of the stored relation only when every binding yields a distinct
+ * tuple, so a count sink must be the head of exactly one rule, whose head lists each of the
+ * rule's variables exactly once, and must appear in no body; orc_run checks this.
+ *
  * Readings of points the paper leaves open (each stated again where used):
  *  - Rounds of a stratum: round 1 evaluates the non-recursive rules of the stratum;
  *    the facts loaded into the stratum's relations join round 1's delta; round t >= 2
@@ -47,10 +60,12 @@
  *  - Results are sets: duplicate facts are dropped; output rows are sorted ascending,
  *    lexicographically over columns 0..arity-1, as unsigned 32-bit values.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #define ORC_MAX_ARITY 8
 #define ORC_MAX_VARS 16
@@ -186,6 +201,9 @@ typedef struct {
     uint32_t* strata_rels;          /* relations of stratum s at [strata_off[s], strata_off[s+1]) */
     uint32_t* strata_off;
     uint32_t* rounds;
+    uint8_t* sink;                  /* 1: count sink (count + digest, no tuples kept) */
+    uint64_t* sink_acc;             /* per relation: count, sum, xor of the row hashes */
+    double join_seconds;            /* time spent in the nested loops (index builds excluded) */
     char err[256];
 } program;
 
@@ -212,6 +230,7 @@ void orc_destroy(void* h) {
         table_free(&p->full[r]); table_free(&p->delta[r]); table_free(&p->fresh[r]);
     }
     free(p->full); free(p->delta); free(p->fresh); free(p->arity); free(p->rules);
+    free(p->sink); free(p->sink_acc);
     free_strata(p);
     free(p);
 }
@@ -226,6 +245,10 @@ int orc_relation(void* h, uint32_t arity) {
     p->full = (table*)realloc(p->full, p->nrel * sizeof(table));
     p->delta = (table*)realloc(p->delta, p->nrel * sizeof(table));
     p->fresh = (table*)realloc(p->fresh, p->nrel * sizeof(table));
+    p->sink = (uint8_t*)realloc(p->sink, p->nrel);
+    p->sink_acc = (uint64_t*)realloc(p->sink_acc, p->nrel * 3 * sizeof(uint64_t));
+    p->sink[r] = 0;
+    p->sink_acc[3 * r] = p->sink_acc[3 * r + 1] = p->sink_acc[3 * r + 2] = 0;
     p->arity[r] = arity;
     table_init(&p->full[r], arity);
     table_init(&p->delta[r], arity);
@@ -233,9 +256,29 @@ int orc_relation(void* h, uint32_t arity) {
     return (int)r;
 }
 
+/* Mark a relation as a count sink (see the header comment). */
+int orc_set_count_sink(void* h, int rel) {
+    program* p = (program*)h;
+    if (rel < 0 || (uint32_t)rel >= p->nrel) return fail(p, "bad relation");
+    if (p->full[rel].n) return fail(p, "a count sink holds no facts");
+    p->sink[rel] = 1;
+    return 0;
+}
+
+/* Count and digest (sum, xor) of a count sink after orc_run. */
+int orc_sink_digest(void* h, int rel, uint64_t* out3) {
+    program* p = (program*)h;
+    if (rel < 0 || (uint32_t)rel >= p->nrel || !p->sink[rel]) return fail(p, "not a count sink");
+    memcpy(out3, p->sink_acc + 3 * rel, 3 * sizeof(uint64_t));
+    return 0;
+}
+
+double orc_join_seconds(void* h) { return ((program*)h)->join_seconds; }
+
 int orc_add_facts(void* h, int rel, const uint32_t* rows, uint64_t n) {
     program* p = (program*)h;
     if (rel < 0 || (uint32_t)rel >= p->nrel) return fail(p, "bad relation");
+    if (p->sink[rel] && n) return fail(p, "a count sink holds no facts");
     for (uint64_t i = 0; i < n; i++) table_insert(&p->full[rel], rows + i * p->arity[rel]);
     return 0;
 }
@@ -488,14 +531,34 @@ typedef struct {
     hindex idx[ORC_MAX_BODY];
     uint32_t bound_at[ORC_MAX_BODY][ORC_MAX_ARITY];  /* 1 if column is a lookup key */
     uint32_t vals[ORC_MAX_VARS];
+    uint32_t ncheck[ORC_MAX_BODY];                   /* comparisons first fully bound at atom k */
+    uint32_t check[ORC_MAX_BODY][ORC_MAX_CMP];
     table* out;
+    uint64_t* sink_acc;                              /* non-NULL: count sink accumulators */
 } join_ctx;
+
+/* Does comparison c hold for the current values (all its variables bound)? */
+static int cmp_holds(const comparison* q, const uint32_t* vals) {
+    const uint32_t a = q->a.kind == T_CONST ? q->a.val : vals[q->a.val];
+    const uint32_t b = q->b.kind == T_CONST ? q->b.val : vals[q->b.val];
+    if (q->op == CMP_LT) return a < b;
+    if (q->op == CMP_LE) return a <= b;
+    return a != b;
+}
 
 static void emit_head(join_ctx* j) {
     uint32_t tup[ORC_MAX_ARITY];
     const atom* h = &j->r->head;
     if (!filters_hold(j->p, j->r, j->vals)) return;
     for (uint32_t c = 0; c < h->arity; c++) tup[c] = h->t[c].kind == T_CONST ? h->t[c].val : j->vals[h->t[c].val];
+    if (j->sink_acc) {
+        /* count sink: every binding is a distinct tuple (checked in orc_run) */
+        const uint64_t x = hash_vals(tup, h->arity);
+        j->sink_acc[0] += 1;
+        j->sink_acc[1] += x;
+        j->sink_acc[2] ^= x;
+        return;
+    }
     table_insert(j->out, tup);
 }
 
@@ -524,18 +587,28 @@ static void join_rec(join_ctx* j, uint32_t k, uint8_t* bound) {
             j->vals[v] = row[c];
             newly[nnew++] = v;
         }
+        /* comparisons whose last variable this atom binds are checked here already */
+        for (uint32_t q = 0; q < j->ncheck[k] && ok; q++) ok = cmp_holds(&j->r->cmp[j->check[k][q]], j->vals);
         if (ok) join_rec(j, k + 1, bound);
         for (uint32_t q = 0; q < nnew; q++) bound[newly[q]] = 0;
     }
 }
 
-/* Evaluate one rule: atom k reads srcs[k]; every derived head tuple goes into out. */
+static double now_seconds(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* Evaluate one rule: atom k reads srcs[k]; every derived head tuple goes into out (or into
+ * the head's count-sink accumulators). */
 static void eval_rule(program* p, const rule* r, const table* const* srcs, table* out) {
     join_ctx j;
     memset(&j, 0, sizeof(j));
     j.p = p;
     j.r = r;
     j.out = out;
+    if (p->sink[r->head.rel]) j.sink_acc = p->sink_acc + 3 * r->head.rel;
     uint8_t bound_before[ORC_MAX_VARS] = {0};
     for (uint32_t k = 0; k < r->nbody; k++) {
         const atom* a = &r->body[k];
@@ -552,8 +625,24 @@ static void eval_rule(program* p, const rule* r, const table* const* srcs, table
         j.src[k] = srcs[k];
         hindex_build(&j.idx[k], srcs[k], cols, nc);
     }
+    /* comparison c is checked at the first atom after which all its variables are bound */
+    for (uint32_t c = 0; c < r->ncmp; c++) {
+        uint8_t seen[ORC_MAX_VARS] = {0};
+        for (uint32_t k = 0; k < r->nbody; k++) {
+            for (uint32_t q = 0; q < r->body[k].arity; q++)
+                if (r->body[k].t[q].kind == T_VAR) seen[r->body[k].t[q].val] = 1;
+            const term* a = &r->cmp[c].a;
+            const term* b = &r->cmp[c].b;
+            if ((a->kind == T_CONST || seen[a->val]) && (b->kind == T_CONST || seen[b->val])) {
+                j.check[k][j.ncheck[k]++] = c;
+                break;
+            }
+        }
+    }
     uint8_t bound[ORC_MAX_VARS] = {0};
+    const double t0 = now_seconds();
     join_rec(&j, 0, bound);
+    p->join_seconds += now_seconds() - t0;
     for (uint32_t k = 0; k < r->nbody; k++) hindex_free(&j.idx[k]);
 }
 
@@ -714,9 +803,42 @@ static uint32_t naive_iterate(program* p, const domain* d, int32_t stratum) {
 
 /* ------------------------------------------------------------------ driver */
 
+/* A count sink must be the head of exactly one rule, whose head lists each of the rule's
+ * variables exactly once, and must appear in no rule body. */
+static int check_sinks(program* p) {
+    for (uint32_t R = 0; R < p->nrel; R++) {
+        if (!p->sink[R]) continue;
+        uint32_t heads = 0;
+        for (uint32_t i = 0; i < p->nrule; i++) {
+            const rule* r = &p->rules[i];
+            for (uint32_t b = 0; b < r->nbody + r->nneg; b++) {
+                const atom* a = b < r->nbody ? &r->body[b] : &r->neg[b - r->nbody];
+                if ((uint32_t)a->rel == R) return fail(p, "a count sink is read by a rule body");
+            }
+            if ((uint32_t)r->head.rel != R) continue;
+            heads++;
+            uint8_t seen[ORC_MAX_VARS] = {0};
+            if (r->head.arity != r->nvars) return fail(p, "a count sink's head must list every rule variable once");
+            for (uint32_t c = 0; c < r->head.arity; c++) {
+                if (r->head.t[c].kind != T_VAR || seen[r->head.t[c].val])
+                    return fail(p, "a count sink's head must list every rule variable once");
+                seen[r->head.t[c].val] = 1;
+            }
+        }
+        if (heads != 1) return fail(p, "a count sink needs exactly one rule");
+        p->sink_acc[3 * R] = p->sink_acc[3 * R + 1] = p->sink_acc[3 * R + 2] = 0;
+    }
+    return 0;
+}
+
 int orc_run(void* h, int mode) {
     program* p = (program*)h;
+    p->join_seconds = 0;
+    if (check_sinks(p)) return -1;
     if (stratify(p)) return -1;
+    if (mode != ORC_SEMINAIVE)
+        for (uint32_t R = 0; R < p->nrel; R++)
+            if (p->sink[R]) return fail(p, "count sinks need the semi-naive mode");
     if (mode == ORC_NAIVE_GLOBAL)
         for (uint32_t i = 0; i < p->nrule; i++)
             if (p->rules[i].nneg) return fail(p, "global naive iteration is undefined for negation");
