@@ -55,6 +55,14 @@ extern "C" {
                                      (the naive assignment ablated in Section 7.3) */
 #define DL_FLAG_DEBUG_CHECKS 0x2u /* re-verify sortedness/uniqueness of every index after each round */
 #define DL_FLAG_PROFILE 0x4u      /* time every kernel launch with CUDA events (dl_stats.kernels) */
+#define DL_FLAG_AUTOTUNE 0x8u     /* autotuner: the first time a join level of a given rule and size
+                                     bucket (log2 of its work units and of its frontier entries)
+                                     runs, its count pass is timed with every candidate tile size
+                                     (4096, 16384, 65536 units per CTA) and kernel shape (a thread per
+                                     unit, or a warp per entry range), and the fastest is kept for
+                                     every later run of that bucket (dl_config.tune_cache keeps the
+                                     choices across engines); ignored when dl_config.tile_units is
+                                     set.  Results never depend on the choice */
 
 typedef struct dl_engine dl_engine;
 typedef uint32_t dl_rel_id;
@@ -87,6 +95,15 @@ typedef struct dl_config {
                                  that a join probe into its rows that needs no narrowed range is
                                  one bit test; 0 = default (512), UINT32_MAX = never.  Bitmaps
                                  take at most 1 GiB per index and a quarter of the budget left */
+    uint64_t frontier_bytes;  /* a join level whose next frontier (the surviving prefixes and
+                                 their carried ranges) would take more than this many bytes
+                                 processes its input prefixes in slices, each carried through
+                                 the remaining levels before the next, so that memory follows
+                                 one slice's frontier; 0 = default (a third of the budget left
+                                 at that point, at least 64 MiB) */
+    const char* tune_cache;   /* DL_FLAG_AUTOTUNE: text file of tuned choices, read when the
+                                 engine is created (if it exists) and rewritten when it is
+                                 destroyed or by dl_tune_save; NULL = choices kept in memory */
 } dl_config;
 
 /* Batched form (dl_config.instances = N >= 1).  The engine holds N independent instances
@@ -262,6 +279,9 @@ typedef struct dl_kernel_stat {
                                * for a radix pass 4*n (histogram) or (4 + 8*arity)*n
                                * (scatter); for dedup / anti-join 4*arity*n read (twice for
                                * dedup) plus 4*arity*kept rows written */
+    uint64_t units;           /* join passes: candidates of the smallest source of every frontier
+                               * entry (T above), summed over the launches */
+    uint64_t entries;         /* join passes: frontier entries (F above), summed */
 } dl_kernel_stat;
 
 typedef struct dl_stats {
@@ -286,6 +306,10 @@ typedef struct dl_stats {
                                   >= dl_config.hub_rows rows, so that a join probe into them that needs
                                   no narrowed range is one bit test (implementation detail,
                                   reported for tests and tuning) */
+    uint32_t join_slices;      /* join levels whose input prefixes were processed in slices
+                                  (dl_config.frontier_bytes) */
+    uint32_t tuned_levels;     /* DL_FLAG_AUTOTUNE: join levels tuned by this call (new buckets) */
+    uint32_t tune_hits;        /* DL_FLAG_AUTOTUNE: join levels that used a cached choice */
 } dl_stats;
 
 /* Evaluate all rules to the least fixpoint (semi-naive, Jacobi rounds: every rule of a
@@ -444,6 +468,12 @@ int dl_server_result(dl_server* s, uint64_t ticket, dl_engine** engine);
 int dl_server_release(dl_server* s, uint64_t ticket);
 
 int dl_server_get_stats(dl_server* s, dl_server_stats* out);
+
+/* Write the autotuner's choices (DL_FLAG_AUTOTUNE) to a text file, one per line: the key
+ * (rule shape hash, level, log2 of units and entries, sources, filters), the tile size, the
+ * kernel shape (1 = a warp per entry range) and the count pass's time in ms when chosen.
+ * Errors: DL_ERR_ARG (NULL path), DL_ERR_STATE (the file cannot be written). */
+int dl_tune_save(dl_engine* e, const char* path);
 
 /* ------------------------------------------------- allocation-free sort + dedup */
 

@@ -31,6 +31,7 @@ ERR_NAMES = {1: "DL_ERR_ARG", 2: "DL_ERR_UNSUPPORTED", 3: "DL_ERR_CAPACITY", 4: 
 DL_FLAG_NAIVE_ROOTS = 0x1
 DL_FLAG_DEBUG_CHECKS = 0x2
 DL_FLAG_PROFILE = 0x4
+DL_FLAG_AUTOTUNE = 0x8
 KERNEL_KINDS = ["join_hist", "join_count", "join_write", "scan", "sort", "delta", "merge", "other"]
 DL_SINK_STORE, DL_SINK_COUNT = 0, 1
 DL_TERM_VAR, DL_TERM_CONST = 0, 1
@@ -48,7 +49,8 @@ class dl_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
                 ("alloc", DL_ALLOC_FN), ("free", DL_FREE_FN), ("alloc_user", ctypes.c_void_p),
                 ("flags", ctypes.c_uint32), ("tile_units", ctypes.c_uint32), ("instances", ctypes.c_uint32),
-                ("chunk_rows", ctypes.c_uint64), ("hub_rows", ctypes.c_uint32)]
+                ("chunk_rows", ctypes.c_uint64), ("hub_rows", ctypes.c_uint32),
+                ("frontier_bytes", ctypes.c_uint64), ("tune_cache", ctypes.c_char_p)]
 
 
 class dl_term(ctypes.Structure):
@@ -64,7 +66,8 @@ class dl_atom(ctypes.Structure):
 
 
 class dl_kernel_stat(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("alg_bytes", ctypes.c_uint64)]
+    _fields_ = [("launches", ctypes.c_uint64), ("ms", ctypes.c_double), ("alg_bytes", ctypes.c_uint64),
+                ("units", ctypes.c_uint64), ("entries", ctypes.c_uint64)]
 
 
 class dl_stats(ctypes.Structure):
@@ -75,7 +78,8 @@ class dl_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_join", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("ms_dedup", ctypes.c_double), ("ms_merge", ctypes.c_double),
                 ("kernels", dl_kernel_stat * len(KERNEL_KINDS)), ("top_kind", ctypes.c_uint32),
-                ("top", dl_kernel_stat), ("hub_keys", ctypes.c_uint32)]
+                ("top", dl_kernel_stat), ("hub_keys", ctypes.c_uint32),
+                ("join_slices", ctypes.c_uint32), ("tuned_levels", ctypes.c_uint32), ("tune_hits", ctypes.c_uint32)]
 
 
 class dl_server_config(ctypes.Structure):
@@ -156,6 +160,7 @@ _SIGS = {
     "dl_server_result": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]),
     "dl_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "dl_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_server_stats)]),
+    "dl_tune_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "dl_sort_unique_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32, ctypes.c_uint64,
                                               ctypes.POINTER(ctypes.c_void_p), _u64p, ctypes.c_void_p]),
 }
@@ -205,7 +210,8 @@ class Engine:
     """One engine handle (owns all of its device memory)."""
 
     def __init__(self, device: int = 0, stream=None, arena_bytes: int = 0, flags: int = 0, tile_units: int = 0,
-                 use_torch_allocator: bool = False, instances: int = 0, chunk_rows: int = 0, hub_rows: int = 0):
+                 use_torch_allocator: bool = False, instances: int = 0, chunk_rows: int = 0, hub_rows: int = 0,
+                 frontier_bytes: int = 0, tune_cache: str | None = None):
         import torch  # plumbing only: stream handle and (optionally) the caching allocator
         self.lib = load_library()
         if not torch.cuda.is_available():
@@ -223,6 +229,9 @@ class Engine:
         cfg.instances = instances
         cfg.chunk_rows = chunk_rows
         cfg.hub_rows = hub_rows
+        cfg.frontier_bytes = frontier_bytes
+        self._tune_cache = tune_cache.encode() if tune_cache else None   # kept alive for the engine
+        cfg.tune_cache = self._tune_cache
         self.instances = instances
         self._cb = None
         if use_torch_allocator:
@@ -293,6 +302,12 @@ class Engine:
         rows = np.asarray(rows, dtype=np.uint32).reshape(-1, self.arity[name])
         cols = [np.ascontiguousarray(rows[:, c]) for c in range(rows.shape[1])]
         self._check(self.lib.dl_load_facts_instance(self.h, self.rel_ids[name], inst, _cols_ptrs(cols), rows.shape[0]))
+
+    def size_instance(self, name: str, inst: int) -> int:
+        """Batched form: rows of one instance's relation."""
+        n = ctypes.c_uint64()
+        self._check(self.lib.dl_fetch_instance(self.h, self.rel_ids[name], inst, None, 0, ctypes.byref(n)))
+        return n.value
 
     def fetch_instance(self, name: str, inst: int) -> np.ndarray:
         n = ctypes.c_uint64()
@@ -391,11 +406,17 @@ class Engine:
         self._check(self.lib.dl_fixpoint(self.h, ctypes.byref(st)))
         out = {f: getattr(st, f) for f, _ in dl_stats._fields_
                if f not in ("rounds", "stratum_first_rel", "kernels", "top", "top_kind")}
-        out["top"] = {"kind": KERNEL_KINDS[st.top_kind], "ms": st.top.ms, "alg_bytes": st.top.alg_bytes}
+        out["top"] = {"kind": KERNEL_KINDS[st.top_kind], "ms": st.top.ms, "alg_bytes": st.top.alg_bytes,
+                      "units": st.top.units, "entries": st.top.entries}
         out["rounds"] = list(st.rounds[: min(st.nstrata, DL_MAX_STRATA)])
         out["kernels"] = {k: {"launches": st.kernels[i].launches, "ms": st.kernels[i].ms,
-                              "alg_bytes": st.kernels[i].alg_bytes} for i, k in enumerate(KERNEL_KINDS)}
+                              "alg_bytes": st.kernels[i].alg_bytes, "units": st.kernels[i].units,
+                              "entries": st.kernels[i].entries} for i, k in enumerate(KERNEL_KINDS)}
         return out
+
+    def tune_save(self, path: str):
+        """Write the autotuner's choices (DL_FLAG_AUTOTUNE) to a text file."""
+        self._check(self.lib.dl_tune_save(self.h, path.encode()))
 
     def strata(self) -> list:
         out = []

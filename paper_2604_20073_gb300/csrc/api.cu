@@ -2,6 +2,7 @@
 // rounds (paper Sections 2 and 4), fetch.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -81,7 +82,29 @@ void Engine::phase_end(int kind) {
     phases.ev[kind].back().second = b;
 }
 
+// Autotuner cache file: "key tile wm ms" per line.
+void tune_load(Engine& E, const std::string& path) {
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char key[128];
+    unsigned tile = 0;
+    int wm = 0;
+    float ms = 0;
+    while (fscanf(f, "%127s %u %d %f", key, &tile, &wm, &ms) == 4)
+        if (tile >= 32 && tile <= (1u << 24)) E.tune[key] = {tile, wm != 0, ms};
+    fclose(f);
+}
+
+bool tune_write(const Engine& E, const std::string& path) {
+    FILE* f = fopen(path.c_str(), "w");
+    if (!f) return false;
+    for (const auto& kv : E.tune) fprintf(f, "%s %u %d %.3f\n", kv.first.c_str(), kv.second.tile, kv.second.wm ? 1 : 0,
+                                          kv.second.ms);
+    return fclose(f) == 0;
+}
+
 Engine::~Engine() {
+    if (!tune_path.empty() && tuned_levels) tune_write(*this, tune_path);
     rels.clear();                      // stream-ordered frees: no wait needed
     for (auto ev : event_pool) cudaEventDestroy(ev);
     if (pool) {
@@ -634,7 +657,8 @@ void validate_program(Engine& E) {
 void fixpoint(Engine& E, dl_stats* st) {
     auto t0 = std::chrono::steady_clock::now();
     const uint64_t launches0 = E.launches;
-    const uint64_t hub0 = E.hub_keys;
+    const uint64_t hub0 = E.hub_keys, slices0 = E.join_slices;
+    const uint64_t tuned0 = E.tuned_levels, hits0 = E.tune_hits;
     E.join_rows = E.count_rows = E.delta_rows = 0;
     E.peak = E.used;
     E.event_next = 0;
@@ -757,6 +781,9 @@ void fixpoint(Engine& E, dl_stats* st) {
         st->peak_bytes = E.peak;
         st->kernel_launches = E.launches - launches0;
         st->hub_keys = (uint32_t)(E.hub_keys - hub0);
+        st->join_slices = (uint32_t)(E.join_slices - slices0);
+        st->tuned_levels = (uint32_t)(E.tuned_levels - tuned0);
+        st->tune_hits = (uint32_t)(E.tune_hits - hits0);
         double* ms[4] = {&st->ms_join, &st->ms_sort, &st->ms_dedup, &st->ms_merge};
         for (int k = 0; k < 4; k++)
             for (auto& pr : E.phases.ev[k]) {
@@ -769,11 +796,15 @@ void fixpoint(Engine& E, dl_stats* st) {
             if (cudaEventElapsedTime(&f, ke.a, ke.b) != cudaSuccess) continue;
             st->kernels[ke.kind].ms += f;
             st->kernels[ke.kind].alg_bytes += ke.bytes;
+            st->kernels[ke.kind].units += ke.units;
+            st->kernels[ke.kind].entries += ke.entries;
             if (f > st->top.ms) {
                 st->top_kind = (uint32_t)ke.kind;
                 st->top.launches = 1;
                 st->top.ms = f;
                 st->top.alg_bytes = ke.bytes;
+                st->top.units = ke.units;
+                st->top.entries = ke.entries;
             }
         }
         st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -858,6 +889,11 @@ int dl_engine_create(const dl_config* cfg, dl_engine** out) {
         E->instances = c.instances;
         if (c.chunk_rows) E->chunk_rows = c.chunk_rows;
         if (c.hub_rows) E->hub_rows = c.hub_rows;
+        E->frontier_bytes = c.frontier_bytes;
+        if (c.tune_cache) {
+            E->tune_path = c.tune_cache;
+            tune_load(*E, E->tune_path);
+        }
         if (!E->ualloc) {
             cudaMemPoolProps props;
             memset(&props, 0, sizeof(props));
@@ -1351,6 +1387,13 @@ int dl_instance_rounds(dl_engine* e, uint32_t inst, uint32_t* rounds, uint32_t c
         if (rounds)
             for (uint32_t s = 0; s < E.inst_rounds.size() && s < cap; s++)
                 rounds[s] = E.inst_rounds[s].empty() ? 0 : E.inst_rounds[s][inst];
+    });
+}
+
+int dl_tune_save(dl_engine* e, const char* path) {
+    return guard(e, [&](Engine& E) {
+        if (!path || !*path) throw Error(DL_ERR_ARG, "null path");
+        if (!tune_write(E, path)) throw Error(DL_ERR_STATE, std::string("cannot write ") + path);
     });
 }
 

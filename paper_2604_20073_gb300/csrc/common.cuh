@@ -93,6 +93,7 @@ struct AtomView {               // an index as the join kernels see it
 constexpr uint32_t kHubMinRows = 512;              // default: keys with this many rows get a bitmap
 constexpr uint64_t kHubBitmapBytes = 1024ull << 20; // bitmap memory per index (at most)
 
+
 struct TableView {              // a plain SoA table (not necessarily sorted)
     uint32_t* col[kMaxArity];
     uint64_t n;

@@ -3,6 +3,7 @@
 
 #include <array>
 #include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -66,6 +67,13 @@ struct KernelEvent {
     int kind;
     cudaEvent_t a, b;
     uint64_t bytes;
+    uint64_t units, entries;          // join passes: candidates of the smallest sources, frontier entries
+};
+
+struct TuneChoice {                   // autotuner: a join level's tile size and kernel shape
+    uint32_t tile = 0;
+    bool wm = false;
+    float ms = 0;                     // the count pass's time when it was chosen
 };
 
 class Engine {
@@ -95,6 +103,11 @@ class Engine {
     uint64_t hub_keys = 0;          // heavy keys given membership bitmaps
     uint32_t hub_rows = kHubMinRows;  // rows that make a key heavy
     uint64_t join_rows = 0, count_rows = 0, delta_rows = 0;
+    uint64_t frontier_bytes = 0;      // join frontier bytes before slicing (0: a third of the budget left)
+    uint64_t join_slices = 0;         // levels whose input was processed in slices
+    std::map<std::string, TuneChoice> tune;   // DL_FLAG_AUTOTUNE: choices by rule, level and size bucket
+    std::string tune_path;            // file the choices are loaded from and saved to ("" = none)
+    uint64_t tuned_levels = 0, tune_hits = 0;
     bool in_fixpoint = false;
     std::vector<cudaEvent_t> event_pool;
     size_t event_next = 0;
@@ -127,9 +140,10 @@ class Engine {
 struct KernelScope {
     Engine& E;
     int kind;
-    uint64_t bytes;
+    uint64_t bytes, units, entries;
     cudaEvent_t a = nullptr;
-    KernelScope(Engine& e, int k, uint64_t b, int nlaunch = 1) : E(e), kind(k), bytes(b) {
+    KernelScope(Engine& e, int k, uint64_t b, int nlaunch = 1, uint64_t u = 0, uint64_t ent = 0)
+        : E(e), kind(k), bytes(b), units(u), entries(ent) {
         E.launches += nlaunch;
         E.klaunch[k] += nlaunch;
         if (E.flags & DL_FLAG_PROFILE) {
@@ -141,7 +155,7 @@ struct KernelScope {
         if (a) {
             cudaEvent_t b = E.next_event();
             cudaEventRecord(b, E.stream);
-            E.kev.push_back({kind, a, b, bytes});
+            E.kev.push_back({kind, a, b, bytes, units, entries});
         }
     }
 };

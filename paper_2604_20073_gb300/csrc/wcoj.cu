@@ -29,6 +29,8 @@
 //    that prefix, i.e. the values of the entry's siblings in the frontier.  Level i+1 then
 //    reads that sibling run as one already-intersected source instead of re-intersecting.
 #include <algorithm>
+#include <cstdio>
+#include <string>
 
 #include "engine.h"
 
@@ -60,9 +62,11 @@ struct LevelParams {
     const uint32_t* fval[kMaxVars];
     const uint32_t* flo[kMaxAtoms];
     const uint32_t* fhi[kMaxAtoms];
+    const uint32_t* sibcol;               // the previous level's values, indexed as the sibling runs are
     const uint32_t* seg;                  // sibling run of each entry: inclusive segment number
     const uint32_t* segstart;             // first entry of each segment (+ end sentinel)
     unsigned long long* C;                // per entry: W, then inclusive prefix
+    unsigned long long* tmin;             // histogram: sum over entries of the smallest source size
     uint8_t* drv;                         // per entry: driving source
     uint64_t T;
     uint64_t tile;
@@ -124,7 +128,7 @@ __device__ __forceinline__ const uint32_t* src_range(const LevelParams& P, int s
         const uint32_t g = __ldg(P.seg + e) - 1;
         lo = __ldg(P.segstart + g);
         hi = __ldg(P.segstart + g + 1);
-        return P.fval[P.level - 1];
+        return P.sibcol;
     }
     const int d = P.src_depth[s];
     if (d == 0) {
@@ -144,26 +148,35 @@ __device__ __forceinline__ const uint32_t* src_range(const LevelParams& P, int s
     return P.atom[a].col[d];
 }
 
+// Histogram (Algorithm 1, Phase 1, at every level): each entry's work W = the size of its
+// smallest candidate source, which drives the entry.  The sum of W over the entries is the
+// level's algorithmic work (every candidate of the smallest source is examined once).
 __global__ void k_wcoj_hist(const __grid_constant__ LevelParams P) {
     const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (e >= P.nF) return;
-    unsigned long long best = ~0ull;
-    uint32_t bs = 0;
-    for (uint32_t s = 0; s < P.nsrc; s++) {
-        const int a = P.src_atom[s], d = P.src_depth[s];
-        unsigned long long len;
-        if (a != kVirtual && d == 0) {
-            const AtomView& A = P.atom[a];
-            len = A.n == 0 ? 0 : (A.root ? A.V : A.n);
-        } else {
-            uint32_t lo, hi;
-            src_range(P, (int)s, e, lo, hi);
-            len = hi - lo;
+    unsigned long long w = 0;
+    if (e < P.nF) {
+        unsigned long long best = ~0ull;
+        uint32_t bs = 0;
+        for (uint32_t s = 0; s < P.nsrc; s++) {
+            const int a = P.src_atom[s], d = P.src_depth[s];
+            unsigned long long len;
+            if (a != kVirtual && d == 0) {
+                const AtomView& A = P.atom[a];
+                len = A.n == 0 ? 0 : (A.root ? A.V : A.n);
+            } else {
+                uint32_t lo, hi;
+                src_range(P, (int)s, e, lo, hi);
+                len = hi - lo;
+            }
+            if (len < best) { best = len; bs = s; }
         }
-        if (len < best) { best = len; bs = s; }
+        w = best == ~0ull ? 0 : best;
+        P.C[e] = w;
+        P.drv[e] = (uint8_t)bs;
     }
-    P.C[e] = best == ~0ull ? 0 : best;
-    P.drv[e] = (uint8_t)bs;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(P.tmin, w);
 }
 
 struct Unit {
@@ -904,18 +917,485 @@ bool head_is_order(const Rule& R) {
     return true;
 }
 
+namespace {
+
+// Entry cut points for slicing a level's input entries [0, nF) into s parts of about equal
+// output: the count pass left the exclusive output offset of every count slot (a tile, or a
+// warp's range in a tile) in bc; cut k is the entry holding the unit where output k * total / s
+// begins (that entry starts the next part, so parts hold whole entries).
+__global__ void k_slice_cuts(const unsigned long long* __restrict__ bc, uint64_t ncounts,
+                             const unsigned long long* __restrict__ C, uint64_t nF, uint64_t T, uint64_t tile, int wm,
+                             uint64_t total, uint32_t s, unsigned long long* __restrict__ cuts) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s) return;
+    if (k == 0) {
+        cuts[0] = 0;
+        return;
+    }
+    const uint64_t target = total / s * k + (total % s) * k / s;
+    // last count slot whose first output is <= target
+    uint64_t i = upper_bound_u64((const uint64_t*)bc, 0, ncounts, target);
+    i = i ? i - 1 : 0;
+    uint64_t unit;
+    if (wm) {
+        const uint64_t per = (tile + kWarps - 1) / kWarps;
+        unit = (i / kWarps) * tile + (i % kWarps) * per;
+    } else {
+        unit = i * tile;
+    }
+    if (unit > T) unit = T;
+    cuts[k] = unit >= T ? nF : upper_bound_u64((const uint64_t*)C, 0, nF, unit);
+}
+
+// Autotuner key: the rule's shape (relation names, terms, variable order), the level, and the
+// size bucket of its work (log2 of the units and of the frontier entries), its source count
+// and whether it filters.
+std::string tune_key(const Rule& R, uint32_t lvl, uint64_t T, uint64_t nF, uint32_t nsrc, bool filt) {
+    uint64_t h = 1469598103934665603ull;   // FNV-1a over the rule's structure
+    auto mixin = [&](uint64_t v) {
+        for (int k = 0; k < 8; k++) {
+            h ^= (v >> (8 * k)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    };
+    auto atom = [&](const RuleAtom& a) {
+        mixin(a.rel);
+        mixin(a.arity);
+        for (uint32_t c = 0; c < a.arity; c++) {
+            mixin(a.terms[c].kind);
+            mixin(a.terms[c].id);
+        }
+    };
+    atom(R.head);
+    for (const RuleAtom& a : R.body) atom(a);
+    for (const RuleAtom& a : R.neg) atom(a);
+    for (uint32_t v : R.order) mixin(v);
+    for (const RuleCmp& q : R.cmps) {
+        mixin(q.op);
+        mixin(q.a.id);
+        mixin(q.b.id);
+    }
+    auto lg = [](uint64_t x) { return x ? 63 - __builtin_clzll(x) : 0; };
+    char buf[128];
+    snprintf(buf, sizeof(buf), "%016llx:L%u:T%d:F%d:S%u:f%d", (unsigned long long)h, lvl, lg(T), lg(nF), nsrc,
+             filt ? 1 : 0);
+    return buf;
+}
+
+// A join frontier: the surviving prefixes of the levels so far (SoA), the narrowed ranges of
+// the atoms still needed later, and the sibling runs when the next level reuses them.
+struct Frontier {
+    uint64_t n = 1;
+    const uint32_t* vals[kMaxVars] = {nullptr};
+    const uint32_t* lo[kMaxAtoms] = {nullptr};
+    const uint32_t* hi[kMaxAtoms] = {nullptr};
+    const uint32_t* seg = nullptr;
+    const uint32_t* segstart = nullptr;
+    int8_t slot_of[kMaxAtoms];
+    DevPtr own_vals, own_rng, own_seg, own_parent;
+    Frontier() {
+        for (int a = 0; a < kMaxAtoms; a++) slot_of[a] = -1;
+    }
+};
+
+struct JoinRun {
+    Engine& E;
+    const Rule& R;
+    const std::vector<const Index*>& nsrc;
+    Relation& head;
+    JoinOutput& out;
+    Plan plan;
+    std::vector<LevelFilters> lf;
+    bool count_sink = false;
+    LevelParams base;
+
+    JoinRun(Engine& e, const Rule& r, const std::vector<const Index*>& ns, Relation& h, JoinOutput& o)
+        : E(e), R(r), nsrc(ns), head(h), out(o) {}
+
+    // Bytes of frontier a level may hold at once before its input entries are processed in
+    // slices (each slice carried through the remaining levels before the next).
+    uint64_t frontier_cap() const {
+        if (E.frontier_bytes) return E.frontier_bytes;
+        const uint64_t left = E.budget > E.used ? E.budget - E.used : 0;
+        return std::max<uint64_t>(64ull << 20, left / 3);
+    }
+
+    // Level lvl over the input entries [ea, eb) of frontier F.
+    void level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb);
+};
+
+void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
+    const uint64_t nF = eb - ea;
+    if (nF == 0) return;
+    const bool last = lvl + 1 == plan.m;
+    const uint32_t reuse = plan.reuse_mask[lvl];
+    const uint32_t defer = plan.defer_mask[lvl];
+    const uint32_t next_reuse = last ? 0 : plan.reuse_mask[lvl + 1];
+    LevelParams P = base;
+    P.level = lvl;
+    P.nF = nF;
+    // per-entry inputs are read at entry - ea; a sibling run's values keep the frontier's own
+    // indexing (runs may extend past the slice)
+    for (uint32_t k = 0; k < lvl; k++) P.fval[k] = F.vals[k] + ea;
+    P.sibcol = lvl ? F.vals[lvl - 1] : nullptr;
+    for (uint32_t a = 0; a < plan.natoms; a++) {
+        P.slot_in[a] = F.slot_of[a];
+        if (F.slot_of[a] >= 0) {
+            P.flo[F.slot_of[a]] = F.lo[F.slot_of[a]] + ea;
+            P.fhi[F.slot_of[a]] = F.hi[F.slot_of[a]] + ea;
+        }
+    }
+    P.seg = F.seg ? F.seg + ea : nullptr;
+    P.segstart = F.segstart;
+    {   // this level's filters
+        const LevelFilters& L = lf[lvl];
+        P.ncmp = (uint32_t)L.op.size();
+        P.nneg = (uint32_t)L.neg.size();
+        for (uint32_t f = 0; f < P.ncmp; f++) {
+            P.cmp_op[f] = L.op[f];
+            P.cmp_pos[f] = L.pos[f];
+            P.cmp_const[f] = L.cst[f];
+        }
+        for (uint32_t k = 0; k < P.nneg; k++) {
+            const int n = L.neg[k];
+            const Perm np = neg_perm(R, (uint32_t)n);
+            P.neg[k] = atom_of(*nsrc[n]);
+            for (uint32_t c = 0; c < R.neg[n].arity; c++)
+                P.neg_pos[k][c] = (int8_t)(std::find(R.order.begin(), R.order.end(), R.neg[n].terms[np[c]].id) -
+                                           R.order.begin());
+        }
+    }
+    // sources of this level (atoms covered by candidate reuse become one sibling source)
+    P.nsrc = 0;
+    for (const Src& s : plan.src[lvl]) {
+        if (((reuse | defer) >> s.atom) & 1u) continue;
+        P.src_atom[P.nsrc] = (uint8_t)s.atom;
+        P.src_depth[P.nsrc] = (uint8_t)s.depth;
+        P.src_need_range[P.nsrc] = plan.last_level[s.atom] > (int)lvl ? 1 : 0;
+        P.src_keypos[P.nsrc] = s.depth == 1 ? (int8_t)plan.colpos[s.atom][0] : (int8_t)-1;
+        P.nsrc++;
+    }
+    if (P.nsrc > (uint32_t)kMaxSrc) throw Error(DL_ERR_UNSUPPORTED, "more than 8 body atoms mention one variable");
+    if (reuse) {
+        P.src_atom[P.nsrc] = kVirtual;
+        P.src_depth[P.nsrc] = 0;
+        P.src_need_range[P.nsrc] = 0;
+        P.nsrc++;
+    }
+    // carried atoms: touched at or before this level and still needed later (atoms the next
+    // level replaces by its sibling source are not needed)
+    P.ncarry = 0;
+    if (!last)
+        for (uint32_t a = 0; a < plan.natoms; a++)
+            if (plan.touch_level[a] <= (int)lvl && plan.last_level[a] > (int)lvl && !((next_reuse >> a) & 1u)) {
+                const int c = (int)P.ncarry++;
+                P.carry_atom[c] = (uint8_t)a;
+                P.carry_src[c] = -1;
+                for (uint32_t s = 0; s < P.nsrc; s++)
+                    if (P.src_atom[s] == a) P.carry_src[c] = (int8_t)s;
+                P.carry_slot[c] = F.slot_of[a];
+            }
+
+    // algorithmic bytes of one frontier entry read (values + carried ranges + sibling run)
+    uint32_t nslots_in = 0;
+    for (uint32_t a = 0; a < plan.natoms; a++) nslots_in += F.slot_of[a] >= 0;
+    const uint64_t entry_bytes = 4ull * (lvl + 2 * nslots_in) + (reuse ? 8 : 0);
+
+    // Phase 1: histogram + prefix (C[nF] receives the total, C[nF + 1] the summed smallest
+    // source sizes)
+    auto C = E.array<uint64_t>(nF + 2);
+    auto drv = E.array<uint8_t>(nF);
+    P.C = (unsigned long long*)C.p;
+    P.tmin = (unsigned long long*)(C.p + nF + 1);
+    P.drv = drv.p;
+    E.phase_begin(0);
+    DL_CUDA(cudaMemsetAsync(C.p + nF + 1, 0, sizeof(uint64_t), E.stream));
+    {
+        KernelScope ks(E, DL_K_JOIN_HIST, (entry_bytes + 9) * nF, 1, 0, nF);
+        k_wcoj_hist<<<(unsigned)((nF + 255) / 256), 256, 0, E.stream>>>(P);
+        DL_CHECK_LAUNCH();
+    }
+    scan_u64(E, C.p, nF, true, C.p + nF);
+    const uint64_t* tt = E.readback(C.p + nF, 2);
+    const uint64_t T = tt[0];
+    // algorithmic work of the level: every candidate of each entry's smallest source
+    const uint64_t Tmin = tt[1];
+    if (T == 0) {
+        E.phase_end(0);
+        return;
+    }
+    P.T = T;
+    const bool filt = P.ncmp || P.nneg;
+    // Count pass with a given tile size and kernel shape: per-tile (striped) or per-warp
+    // (warp-major) output counts, plus the count sink's digest at the last level.
+    struct CountRun {
+        uint32_t tile = 0;
+        bool wm = false;
+        uint64_t ntiles = 0, ncounts = 0;
+        DArray<uint64_t> bc, dg;
+        float ms = 0;
+    };
+    if (last && count_sink) {
+        P.mode = MODE_COUNT;
+        P.head_lvl = -1;
+        for (uint32_t c = 0; c < P.head_arity; c++)
+            if (P.head_pos[c] == (int)lvl) P.head_lvl = (int8_t)c;
+        if (P.head_lvl < 0) throw Error(DL_ERR_STATE, "count sink head lacks the last variable");
+    } else {
+        P.mode = last ? MODE_HEAD : MODE_FRONTIER;
+    }
+    auto count_with = [&](uint32_t tile, bool wmk, bool timed) {
+        CountRun r;
+        r.tile = tile;
+        r.wm = wmk;
+        r.ntiles = P.naive ? nF : (T + tile - 1) / tile;
+        if (r.ntiles >= (1ull << 31)) throw Error(DL_ERR_CAPACITY, "join level exceeds 2^31 tiles");
+        r.ncounts = wmk ? r.ntiles * kWarps : r.ntiles;
+        r.bc = E.array<uint64_t>(r.ncounts + 1);
+        P.tile = tile;
+        P.block_count = (unsigned long long*)r.bc.p;
+        if (P.mode == MODE_COUNT) {
+            r.dg = E.array<uint64_t>(3);
+            DL_CUDA(cudaMemsetAsync(r.dg.p, 0, 24, E.stream));
+            P.digest = (unsigned long long*)r.dg.p;
+        }
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timed) {
+            a = E.next_event();
+            b = E.next_event();
+            DL_CUDA(cudaEventRecord(a, E.stream));
+        }
+        {
+            KernelScope ks(E, DL_K_JOIN_COUNT, 4 * Tmin + (entry_bytes + 9) * nF, 1, Tmin, nF);
+            if (wmk) DL_NS_DISPATCH(k_wcoj_count_wm, P.nsrc, filt, (unsigned)r.ntiles, E.stream, P);
+            else if (filt) k_wcoj_count<true><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
+            else k_wcoj_count<false><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
+            DL_CHECK_LAUNCH();
+        }
+        if (timed) {
+            DL_CUDA(cudaEventRecord(b, E.stream));
+            DL_CUDA(cudaEventSynchronize(b));
+            DL_CUDA(cudaEventElapsedTime(&r.ms, a, b));
+        }
+        return r;
+    };
+    // Tile size (units per CTA) and kernel shape: the autotuner's cached choice for this
+    // rule, level and size bucket; on a miss every candidate is timed once and the fastest is
+    // kept (its counts are the ones used); without the autotuner, the fixed heuristic.
+    CountRun cr;
+    bool tuned = false;
+    if ((E.flags & DL_FLAG_AUTOTUNE) && !P.naive && !E.tile_units) {
+        const std::string key = tune_key(R, lvl, T, nF, P.nsrc, filt);
+        auto it = E.tune.find(key);
+        if (it != E.tune.end()) {
+            cr = count_with(it->second.tile, it->second.wm, false);
+            E.tune_hits++;
+        } else {
+            CountRun best;
+            for (uint32_t tile : {4096u, 16384u, 65536u})
+                for (bool wmk : {false, true}) {
+                    CountRun r = count_with(tile, wmk, true);
+                    if (!best.bc.mem || r.ms < best.ms) best = std::move(r);
+                }
+            E.tune[key] = {best.tile, best.wm, best.ms};
+            E.tuned_levels++;
+            cr = std::move(best);
+        }
+        tuned = true;
+    }
+    if (!tuned) {
+        const uint32_t tile = E.tile_units ? E.tile_units : auto_tile(E, T);
+        // warp-major kernels when entries average >= 32 units (one count per warp)
+        cr = count_with(tile, !P.naive && T >= 32 * nF, false);
+    }
+    P.tile = cr.tile;
+    P.block_count = (unsigned long long*)cr.bc.p;
+    const bool wm = cr.wm;
+    const uint64_t ntiles = cr.ntiles, ncounts = cr.ncounts;
+    auto bc = cr.bc;
+    auto launch_write = [&](uint64_t grid) {
+        if (wm) DL_NS_DISPATCH(k_wcoj_write_wm, P.nsrc, filt, (unsigned)grid, E.stream, P);
+        else if (filt) k_wcoj_write<true><<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
+        else k_wcoj_write<false><<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
+    };
+
+    if (last && count_sink) {
+        const uint64_t* d = E.readback(cr.dg.p, 3);
+        head.sink_count += d[0];
+        head.sink_digest[0] += d[1];
+        head.sink_digest[1] ^= d[2];
+        E.count_rows += d[0];
+        E.phase_end(0);
+        return;
+    }
+
+    // Phase 2: count -> exclusive offsets
+    scan_u64(E, bc.p, ncounts, false, bc.p + ncounts);
+    const uint64_t total = E.readback(bc.p + ncounts, 1)[0];
+    if (total == 0) {
+        E.phase_end(0);
+        return;
+    }
+
+    // Phase 3: allocate exactly and write
+    if (last) {
+        E.join_rows += total;
+        // Outputs above chunk_rows are written one tile range at a time; each chunk goes to the
+        // caller's chunk sink (sorted, deduplicated, anti-joined) before the next.
+        std::vector<uint64_t> off;
+        const bool chunked = total > E.chunk_rows && out.chunk_sink;
+        if (total >= (1ull << 32) && !chunked) throw Error(DL_ERR_CAPACITY, "rule output of 2^32 rows or more in one round");
+        if (chunked) {
+            std::vector<uint64_t> all(ncounts + 1);
+            DL_CUDA(cudaMemcpyAsync(all.data(), bc.p, sizeof(uint64_t) * (ncounts + 1), cudaMemcpyDeviceToHost,
+                                    E.stream));
+            E.sync();
+            off.resize(ntiles + 1);   // output offset of each tile's first unit
+            for (uint64_t t = 0; t <= ntiles; t++) off[t] = all[wm ? t * kWarps : t];
+        } else {
+            off = {0, total};
+        }
+        const uint64_t nt = chunked ? ntiles : 1;
+        uint64_t a = 0;
+        while (a < nt) {
+            uint64_t b = chunked ? (uint64_t)(std::upper_bound(off.begin() + a + 1, off.end(), off[a] + E.chunk_rows) -
+                                              off.begin()) - 1
+                                 : 1;
+            if (b <= a) b = a + 1;
+            const uint64_t rows = off[b] - off[a];
+            if (rows) {
+                auto buf = E.make(sizeof(uint32_t) * R.head.arity * rows);
+                TableView tv;
+                memset(&tv, 0, sizeof(tv));
+                tv.arity = R.head.arity;
+                tv.n = rows;
+                for (uint32_t c = 0; c < R.head.arity; c++) {
+                    tv.col[c] = (uint32_t*)buf->ptr + (size_t)c * rows;
+                    P.ocol[c] = tv.col[c];
+                }
+                P.tile_base = chunked ? a : 0;
+                P.out_base = off[a];
+                const uint64_t grid = chunked ? b - a : ntiles;
+                {
+                    KernelScope ks(E, DL_K_JOIN_WRITE,
+                                   (4 * Tmin + (entry_bytes + 9) * nF) * grid / ntiles + 4ull * R.head.arity * rows, 1,
+                                   Tmin * grid / ntiles, nF * grid / ntiles);
+                    launch_write(grid);
+                    DL_CHECK_LAUNCH();
+                }
+                if (chunked) {
+                    out.chunk_sink(buf, tv);
+                } else {
+                    out.parts.push_back(tv);
+                    out.owners.push_back(buf);
+                }
+            }
+            a = b;
+        }
+        E.phase_end(0);
+        return;
+    }
+
+    // The next frontier's bytes per entry (values, carried ranges, parent and sibling runs).
+    const uint64_t bpe = 4ull * (lvl + 1 + 2 * P.ncarry) + (next_reuse ? 12 : 0);
+    if (total * bpe > frontier_cap() && nF > 1) {
+        // Bounded memory: cut the input entries into slices of about equal output and carry
+        // each slice through the remaining levels before the next (the paper's two-phase
+        // allocation applied per slice).
+        const uint64_t want = (total * bpe + frontier_cap() - 1) / frontier_cap();
+        const uint32_t s = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(want, 2), 63);
+        auto cuts = E.array<uint64_t>(64);
+        {
+            KernelScope ks(E, DL_K_OTHER, 8ull * s * 64);
+            k_slice_cuts<<<1, 64, 0, E.stream>>>((const unsigned long long*)bc.p, ncounts, P.C, nF, T, P.tile, wm ? 1 : 0,
+                                                 total, s, (unsigned long long*)cuts.p);
+            DL_CHECK_LAUNCH();
+        }
+        const uint64_t* cutp = E.readback(cuts.p, s);
+        std::vector<uint64_t> cut(cutp, cutp + s);
+        cut.push_back(nF);
+        E.phase_end(0);
+        uint64_t prev = 0;
+        bool split = false;
+        for (uint32_t k = 1; k <= s; k++) {
+            const uint64_t c = std::min<uint64_t>(std::max<uint64_t>(cut[k], prev), nF);
+            if (c > prev && (prev > 0 || c < nF)) split = true;
+            cut[k] = c;
+            prev = c;
+        }
+        if (split) {
+            E.join_slices += 1;
+            C = DArray<uint64_t>();
+            drv = DArray<uint8_t>();
+            bc = DArray<uint64_t>();
+            cr = CountRun();
+            for (uint32_t k = 0; k < s; k++)
+                if (cut[k + 1] > cut[k]) level(lvl, F, ea + cut[k], ea + cut[k + 1]);
+            return;
+        }
+        E.phase_begin(0);   // a single entry holds (nearly) all of the output: no cut possible
+    }
+    if (next_reuse && (nF >= 0xFFFFFFFEull || total >= 0xFFFFFFFEull))
+        throw Error(DL_ERR_CAPACITY, "join frontier of 2^32 - 2 entries or more");
+    Frontier N;
+    N.n = total;
+    N.own_vals = E.make(sizeof(uint32_t) * (lvl + 1) * total);
+    N.own_rng = E.make(sizeof(uint32_t) * 2 * std::max<uint32_t>(1, P.ncarry) * total);
+    for (uint32_t k = 0; k <= lvl; k++) P.oval[k] = (uint32_t*)N.own_vals->ptr + (size_t)k * total;
+    for (uint32_t c = 0; c < P.ncarry; c++) {
+        P.olo[c] = (uint32_t*)N.own_rng->ptr + (size_t)(2 * c) * total;
+        P.ohi[c] = (uint32_t*)N.own_rng->ptr + (size_t)(2 * c + 1) * total;
+    }
+    P.oparent = nullptr;
+    if (next_reuse) {
+        N.own_parent = E.make(sizeof(uint32_t) * total);
+        P.oparent = (uint32_t*)N.own_parent->ptr;
+    }
+    {
+        KernelScope ks(E, DL_K_JOIN_WRITE,
+                       4 * Tmin + (entry_bytes + 9) * nF + 4ull * (lvl + 1 + 2 * P.ncarry + (next_reuse ? 1 : 0)) * total,
+                       1, Tmin, nF);
+        launch_write(ntiles);
+        DL_CHECK_LAUNCH();
+    }
+    if (next_reuse) {
+        N.own_seg = E.make(sizeof(uint32_t) * (2 * total + 1));
+        uint32_t* seg = (uint32_t*)N.own_seg->ptr;
+        uint32_t* segstart = seg + total;
+        launch_seg(E, P.oparent, total, seg, segstart);
+        N.seg = seg;
+        N.segstart = segstart;
+    }
+    E.phase_end(0);
+    for (uint32_t k = 0; k <= lvl; k++) N.vals[k] = P.oval[k];
+    for (uint32_t c = 0; c < P.ncarry; c++) {
+        N.slot_of[P.carry_atom[c]] = (int8_t)c;
+        N.lo[c] = P.olo[c];
+        N.hi[c] = P.ohi[c];
+    }
+    // this level's own buffers are no longer needed below
+    C = DArray<uint64_t>();
+    drv = DArray<uint8_t>();
+    bc = DArray<uint64_t>();
+    cr = CountRun();
+    N.own_parent.reset();
+    level(lvl + 1, N, 0, total);
+}
+
+}  // namespace
+
 void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, const std::vector<const Index*>& nsrc,
               Relation& head, JoinOutput& out) {
-    std::vector<LevelFilters> lf;
+    JoinRun J(E, R, nsrc, head, out);
     uint64_t filter_levels = 0;
-    if (!place_filters(R, nsrc, lf, filter_levels)) return;   // a comparison that never holds
-    const Plan plan = make_plan(R, src, filter_levels);
-    const bool count_sink = head.sink == DL_SINK_COUNT;
+    if (!place_filters(R, nsrc, J.lf, filter_levels)) return;   // a comparison that never holds
+    J.plan = make_plan(R, src, filter_levels);
+    J.count_sink = head.sink == DL_SINK_COUNT;
     out.sorted_unique = head_is_order(R);
 
-    LevelParams P;
+    LevelParams& P = J.base;
     memset(&P, 0, sizeof(P));
-    for (uint32_t a = 0; a < plan.natoms; a++) {
+    for (uint32_t a = 0; a < J.plan.natoms; a++) {
         P.atom[a] = atom_of(*src[a]);
         if (src[a]->n == 0) return;      // an empty atom: the body has no binding
     }
@@ -930,265 +1410,9 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, co
             P.head_pos[c] = (int8_t)(std::find(R.order.begin(), R.order.end(), R.head.terms[c].id) - R.order.begin());
         }
     }
-
-    // frontier state (host handles)
-    uint64_t nF = 1;
-    DevPtr f_vals_owner, f_rng_owner, f_seg_owner;
-    const uint32_t* f_vals[kMaxVars] = {nullptr};
-    const uint32_t* f_lo[kMaxAtoms] = {nullptr};
-    const uint32_t* f_hi[kMaxAtoms] = {nullptr};
-    const uint32_t* f_seg = nullptr;
-    const uint32_t* f_segstart = nullptr;
-    int8_t slot_of[kMaxAtoms];
-    for (int a = 0; a < kMaxAtoms; a++) slot_of[a] = -1;
-    for (uint32_t a = 0; a < plan.natoms; a++) P.lazy_pos[a] = (int8_t)plan.lazy_pos[a];
-
-    auto C = E.array<uint64_t>(1);
-    for (uint32_t lvl = 0; lvl < plan.m; lvl++) {
-        const bool last = lvl + 1 == plan.m;
-        const uint32_t reuse = plan.reuse_mask[lvl];
-        const uint32_t defer = plan.defer_mask[lvl];
-        const uint32_t next_reuse = last ? 0 : plan.reuse_mask[lvl + 1];
-        P.level = lvl;
-        P.nF = nF;
-        for (uint32_t k = 0; k < lvl; k++) P.fval[k] = f_vals[k];
-        for (uint32_t a = 0; a < plan.natoms; a++) {
-            P.slot_in[a] = slot_of[a];
-            if (slot_of[a] >= 0) {
-                P.flo[slot_of[a]] = f_lo[slot_of[a]];
-                P.fhi[slot_of[a]] = f_hi[slot_of[a]];
-            }
-        }
-        P.seg = f_seg;
-        P.segstart = f_segstart;
-        {   // this level's filters
-            const LevelFilters& L = lf[lvl];
-            P.ncmp = (uint32_t)L.op.size();
-            P.nneg = (uint32_t)L.neg.size();
-            for (uint32_t f = 0; f < P.ncmp; f++) {
-                P.cmp_op[f] = L.op[f];
-                P.cmp_pos[f] = L.pos[f];
-                P.cmp_const[f] = L.cst[f];
-            }
-            for (uint32_t k = 0; k < P.nneg; k++) {
-                const int n = L.neg[k];
-                const Perm np = neg_perm(R, (uint32_t)n);
-                P.neg[k] = atom_of(*nsrc[n]);
-                for (uint32_t c = 0; c < R.neg[n].arity; c++)
-                    P.neg_pos[k][c] = (int8_t)(std::find(R.order.begin(), R.order.end(), R.neg[n].terms[np[c]].id) -
-                                               R.order.begin());
-            }
-        }
-        // sources of this level (atoms covered by candidate reuse become one sibling source)
-        P.nsrc = 0;
-        for (const Src& s : plan.src[lvl]) {
-            if (((reuse | defer) >> s.atom) & 1u) continue;
-            P.src_atom[P.nsrc] = (uint8_t)s.atom;
-            P.src_depth[P.nsrc] = (uint8_t)s.depth;
-            P.src_need_range[P.nsrc] = plan.last_level[s.atom] > (int)lvl ? 1 : 0;
-            P.src_keypos[P.nsrc] = s.depth == 1 ? (int8_t)plan.colpos[s.atom][0] : (int8_t)-1;
-            P.nsrc++;
-        }
-        if (P.nsrc > (uint32_t)kMaxSrc)
-            throw Error(DL_ERR_UNSUPPORTED, "more than 8 body atoms mention one variable");
-        if (reuse) {
-            P.src_atom[P.nsrc] = kVirtual;
-            P.src_depth[P.nsrc] = 0;
-            P.src_need_range[P.nsrc] = 0;
-            P.nsrc++;
-        }
-        // carried atoms: touched at or before this level and still needed later (atoms the
-        // next level replaces by its sibling source are not needed)
-        P.ncarry = 0;
-        if (!last)
-            for (uint32_t a = 0; a < plan.natoms; a++)
-                if (plan.touch_level[a] <= (int)lvl && plan.last_level[a] > (int)lvl && !((next_reuse >> a) & 1u)) {
-                    const int c = (int)P.ncarry++;
-                    P.carry_atom[c] = (uint8_t)a;
-                    P.carry_src[c] = -1;
-                    for (uint32_t s = 0; s < P.nsrc; s++)
-                        if (P.src_atom[s] == a) P.carry_src[c] = (int8_t)s;
-                    P.carry_slot[c] = slot_of[a];
-                }
-
-        // algorithmic bytes of one frontier entry read (values + carried ranges + sibling run)
-        uint32_t nslots_in = 0;
-        for (uint32_t a = 0; a < plan.natoms; a++) nslots_in += slot_of[a] >= 0;
-        const uint64_t entry_bytes = 4ull * (lvl + 2 * nslots_in) + (reuse ? 8 : 0);
-
-        // Phase 1: histogram + prefix
-        C = E.array<uint64_t>(nF + 1);
-        auto drv = E.array<uint8_t>(nF);
-        P.C = (unsigned long long*)C.p;
-        P.drv = drv.p;
-        E.phase_begin(0);
-        {
-            KernelScope ks(E, DL_K_JOIN_HIST, (entry_bytes + 9) * nF);
-            k_wcoj_hist<<<(unsigned)((nF + 255) / 256), 256, 0, E.stream>>>(P);
-            DL_CHECK_LAUNCH();
-        }
-        scan_u64(E, C.p, nF, true, C.p + nF);
-        const uint64_t T = E.readback(C.p + nF, 1)[0];
-        if (T == 0) { E.phase_end(0); return; }
-        P.T = T;
-        P.tile = E.tile_units ? E.tile_units : auto_tile(E, T);
-        const uint64_t ntiles = P.naive ? nF : (T + P.tile - 1) / P.tile;
-        if (ntiles >= (1ull << 31)) throw Error(DL_ERR_CAPACITY, "join level exceeds 2^31 tiles");
-        // warp-major kernels when entries average >= 32 units (one count per warp)
-        const bool wm = !P.naive && T >= 32 * nF;
-        const uint64_t ncounts = wm ? ntiles * kWarps : ntiles;
-        auto bc = E.array<uint64_t>(ncounts + 1);
-        P.block_count = (unsigned long long*)bc.p;
-        auto launch_count = [&]() {
-            const bool filt = P.ncmp || P.nneg;
-            if (wm) DL_NS_DISPATCH(k_wcoj_count_wm, P.nsrc, filt, (unsigned)ntiles, E.stream, P);
-            else if (filt) k_wcoj_count<true><<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
-            else k_wcoj_count<false><<<(unsigned)ntiles, kJoinThreads, 0, E.stream>>>(P);
-        };
-        auto launch_write = [&](uint64_t grid) {
-            const bool filt = P.ncmp || P.nneg;
-            if (wm) DL_NS_DISPATCH(k_wcoj_write_wm, P.nsrc, filt, (unsigned)grid, E.stream, P);
-            else if (filt) k_wcoj_write<true><<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
-            else k_wcoj_write<false><<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
-        };
-
-        if (last && count_sink) {
-            auto dg = E.array<uint64_t>(3);
-            DL_CUDA(cudaMemsetAsync(dg.p, 0, 24, E.stream));
-            P.mode = MODE_COUNT;
-            P.digest = (unsigned long long*)dg.p;
-            P.head_lvl = -1;
-            for (uint32_t c = 0; c < P.head_arity; c++)
-                if (P.head_pos[c] == (int)lvl) P.head_lvl = (int8_t)c;
-            if (P.head_lvl < 0) throw Error(DL_ERR_STATE, "count sink head lacks the last variable");
-            {
-                KernelScope ks(E, DL_K_JOIN_COUNT, 4 * T + (entry_bytes + 9) * nF);
-                launch_count();
-                DL_CHECK_LAUNCH();
-            }
-            const uint64_t* d = E.readback(dg.p, 3);
-            head.sink_count += d[0];
-            head.sink_digest[0] += d[1];
-            head.sink_digest[1] ^= d[2];
-            E.count_rows += d[0];
-            E.phase_end(0);
-            return;
-        }
-
-        // Phase 2: count -> exclusive offsets
-        P.mode = last ? MODE_HEAD : MODE_FRONTIER;
-        {
-            KernelScope ks(E, DL_K_JOIN_COUNT, 4 * T + (entry_bytes + 9) * nF);
-            launch_count();
-            DL_CHECK_LAUNCH();
-        }
-        scan_u64(E, bc.p, ncounts, false, bc.p + ncounts);
-        const uint64_t total = E.readback(bc.p + ncounts, 1)[0];
-        if (total == 0) { E.phase_end(0); return; }
-
-        // Phase 3: allocate exactly and write
-        if (last) {
-            E.join_rows += total;
-            // Outputs above chunk_rows are written one tile range at a time; each chunk goes to
-            // the caller's chunk sink (sorted, deduplicated, anti-joined) before the next.
-            std::vector<uint64_t> off;
-            const bool chunked = total > E.chunk_rows && out.chunk_sink;
-            if (total >= (1ull << 32) && !chunked)
-                throw Error(DL_ERR_CAPACITY, "rule output of 2^32 rows or more in one round");
-            if (chunked) {
-                std::vector<uint64_t> all(ncounts + 1);
-                DL_CUDA(cudaMemcpyAsync(all.data(), bc.p, sizeof(uint64_t) * (ncounts + 1), cudaMemcpyDeviceToHost,
-                                        E.stream));
-                E.sync();
-                off.resize(ntiles + 1);   // output offset of each tile's first unit
-                for (uint64_t t = 0; t <= ntiles; t++) off[t] = all[wm ? t * kWarps : t];
-            } else {
-                off = {0, total};
-            }
-            const uint64_t nt = chunked ? ntiles : 1;
-            uint64_t a = 0;
-            while (a < nt) {
-                uint64_t b = chunked ? (uint64_t)(std::upper_bound(off.begin() + a + 1, off.end(), off[a] + E.chunk_rows) -
-                                                  off.begin()) - 1
-                                     : 1;
-                if (b <= a) b = a + 1;
-                const uint64_t rows = off[b] - off[a];
-                if (rows) {
-                    auto buf = E.make(sizeof(uint32_t) * R.head.arity * rows);
-                    TableView tv;
-                    memset(&tv, 0, sizeof(tv));
-                    tv.arity = R.head.arity;
-                    tv.n = rows;
-                    for (uint32_t c = 0; c < R.head.arity; c++) {
-                        tv.col[c] = (uint32_t*)buf->ptr + (size_t)c * rows;
-                        P.ocol[c] = tv.col[c];
-                    }
-                    P.tile_base = chunked ? a : 0;
-                    P.out_base = off[a];
-                    const uint64_t grid = chunked ? b - a : ntiles;
-                    {
-                        KernelScope ks(E, DL_K_JOIN_WRITE,
-                                       (4 * T + (entry_bytes + 9) * nF) * grid / ntiles + 4ull * R.head.arity * rows);
-                        launch_write(grid);
-                        DL_CHECK_LAUNCH();
-                    }
-                    if (chunked) {
-                        out.chunk_sink(buf, tv);
-                    } else {
-                        out.parts.push_back(tv);
-                        out.owners.push_back(buf);
-                    }
-                }
-                a = b;
-            }
-            P.tile_base = P.out_base = 0;
-            E.phase_end(0);
-            return;
-        }
-        if (next_reuse && (nF >= (1ull << 32) || total >= (1ull << 32)))
-            throw Error(DL_ERR_CAPACITY, "join frontier of 2^32 entries or more");
-        auto vals = E.make(sizeof(uint32_t) * (lvl + 1) * total);
-        auto rng = E.make(sizeof(uint32_t) * 2 * std::max<uint32_t>(1, P.ncarry) * total);
-        DevPtr parent, segbuf;
-        for (uint32_t k = 0; k <= lvl; k++) P.oval[k] = (uint32_t*)vals->ptr + (size_t)k * total;
-        for (uint32_t c = 0; c < P.ncarry; c++) {
-            P.olo[c] = (uint32_t*)rng->ptr + (size_t)(2 * c) * total;
-            P.ohi[c] = (uint32_t*)rng->ptr + (size_t)(2 * c + 1) * total;
-        }
-        P.oparent = nullptr;
-        if (next_reuse) {
-            parent = E.make(sizeof(uint32_t) * total);
-            P.oparent = (uint32_t*)parent->ptr;
-        }
-        {
-            KernelScope ks(E, DL_K_JOIN_WRITE,
-                           4 * T + (entry_bytes + 9) * nF + 4ull * (lvl + 1 + 2 * P.ncarry + (next_reuse ? 1 : 0)) * total);
-            launch_write(ntiles);
-            DL_CHECK_LAUNCH();
-        }
-        f_seg = f_segstart = nullptr;
-        if (next_reuse) {
-            segbuf = E.make(sizeof(uint32_t) * (2 * total + 1));
-            uint32_t* seg = (uint32_t*)segbuf->ptr;
-            uint32_t* segstart = seg + total;
-            launch_seg(E, P.oparent, total, seg, segstart);
-            f_seg = seg;
-            f_segstart = segstart;
-        }
-        E.phase_end(0);
-        // the new frontier
-        nF = total;
-        for (uint32_t k = 0; k <= lvl; k++) f_vals[k] = P.oval[k];
-        for (int a = 0; a < kMaxAtoms; a++) slot_of[a] = -1;
-        for (uint32_t c = 0; c < P.ncarry; c++) {
-            slot_of[P.carry_atom[c]] = (int8_t)c;
-            f_lo[c] = P.olo[c];
-            f_hi[c] = P.ohi[c];
-        }
-        f_vals_owner = vals;
-        f_rng_owner = rng;
-        f_seg_owner = segbuf;
-    }
+    for (uint32_t a = 0; a < J.plan.natoms; a++) P.lazy_pos[a] = (int8_t)J.plan.lazy_pos[a];
+    Frontier root;   // the empty prefix
+    J.level(0, root, 0, 1);
 }
 
 }  // namespace dl

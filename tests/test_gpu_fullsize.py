@@ -1,14 +1,23 @@
 """Parity at the full size of the skewed cyclic workload (symmetrised R-MAT scale 20,
 16,777,216 rows), in the launch configuration bench.py times.
 
-The oracle cannot evaluate the whole workload in seconds, so:
+* whole relations against the oracle: the count and order-independent digest of the
+  oriented triangles (TriLt) and 4-cliques (Q4Lt, count sink) and of the symmetric
+  triangles (Tri), from tests/golden/cliques_rmat20.json (written by
+  tests/golden/make_fullsize_cliques.py, which runs only the oracle); the symmetric 4-clique
+  count is 24 x the oracle's oriented count and the symmetric triangle count 6 x (each
+  clique in every order);
 * sampled outputs: Tri and Q4 rows rooted at sampled vertices (the heaviest hubs for Tri,
-  random non-hub vertices for Q4), computed by the GPU and by the oracle as root-restricted
-  programs (Root(x) is one more body atom), compared tuple for tuple;
+  random vertices plus heavy keys with bitmaps for Q4), computed by the GPU and by the
+  oracle as root-restricted programs (Root(x) is one more body atom), compared tuple for
+  tuple;
 * properties that hold at any size, between independent GPU runs: |Tri| on the symmetric
   graph = 6 x |Tri| on the id-oriented graph, |Q4| = 24 x, and the AGM bounds
   |Tri| <= |E|^1.5, |Q4| <= |E|^2 (paper Section 2).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -26,9 +35,37 @@ Q4_R = [(("Q4R", ["w", "x", "y", "z"]),
           ("E", ["x", "z"]), ("E", ["y", "z"])], ["w", "x", "y", "z"])]
 
 
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cliques_rmat20.json")
+TRI_LT = [(("TriLt", ["x", "y", "z"]), [("E", ["x", "y"]), ("E", ["y", "z"]), ("E", ["x", "z"]),
+                                       ("<", "x", "y"), ("<", "y", "z")], ["x", "y", "z"])]
+Q4_LT = [(("Q4Lt", ["w", "x", "y", "z"]), [("E", ["w", "x"]), ("E", ["w", "y"]), ("E", ["w", "z"]),
+                                          ("E", ["x", "y"]), ("E", ["x", "z"]), ("E", ["y", "z"]),
+                                          ("<", "w", "x"), ("<", "x", "y"), ("<", "y", "z")], ["w", "x", "y", "z"])]
+
+
 @pytest.fixture(scope="module")
 def edges():
     return dg.rmat_edges(1 << 20, 1 << 24, 1001, symmetric=True)
+
+
+def test_whole_relations_match_oracle_goldens(edges):
+    gold = json.load(open(GOLDEN))
+    assert gold["graph"] == "rmat_edges(1048576, 16777216, 1001, symmetric=True)"
+    want = {k: (gold[k]["count"], gold[k]["sum"], gold[k]["xor"]) for k in ("TriLt", "Q4Lt", "Tri")}
+    # the oriented rules (comparison filters) and the symmetric ones, as bench.py runs them
+    with pkg.Engine(flags=pkg.DL_FLAG_PROFILE) as eng:
+        pkg.build_program(eng, {"E": 2, "TriLt": 3, "Q4Lt": 4}, TRI_LT + Q4_LT, {"Q4Lt": pkg.DL_SINK_COUNT})
+        eng.load("E", edges)
+        eng.fixpoint()
+        assert eng.digest("TriLt") == want["TriLt"]
+        assert eng.digest("Q4Lt") == want["Q4Lt"]
+    with pkg.Engine(flags=pkg.DL_FLAG_PROFILE) as eng:
+        pkg.build_program(eng, {"E": 2, "Tri": 3, "Q4": 4}, P.TRI + P.Q4, {"Q4": pkg.DL_SINK_COUNT})
+        eng.load("E", edges)
+        eng.fixpoint()
+        assert eng.digest("Tri") == want["Tri"]
+        assert eng.size("Tri") == 6 * want["TriLt"][0]
+        assert eng.size("Q4") == 24 * want["Q4Lt"][0]
 
 
 def test_sampled_roots_match_oracle(edges):
