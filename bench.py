@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="cyclic", choices=["cyclic", "batched", "served", "split", "oriented"],
+    ap.add_argument("--pt-scale", type=float, default=64.0, help="points-to workload: facts at scale 1/pt-scale")
+    ap.add_argument("--workload", default="cyclic",
+                    choices=["cyclic", "batched", "served", "split", "oriented", "points-to"],
                     help="cyclic: the Tri + Q4 fixpoint line (default); batched: 4096 TC+Tri instances; "
                          "served: Poisson request mix through the serving loop; split: helper-relation "
                          "splitting ablation on CallGraphEdge; oriented: Tri + Q4 with comparison filters")
@@ -332,11 +334,19 @@ def batched_measure(instances: int, warmup: int, steps: int) -> dict:
             sizes_b[i] = (eng.size_instance("Tri", j), eng.instance_rounds(j))
     reach_total = sum(eng.size("Reach") for eng in engines)
     tri_total = sum(eng.size("Tri") for eng in engines)
+    rng = np.random.default_rng(5)
+    sample = set(rng.choice(instances, min(16, instances), replace=False).tolist())
+    sample_rows = {}
+    for i in sample:
+        g = next(k for k, gg in enumerate(groups) if i in gg)
+        j = groups[g].index(i)
+        sample_rows[i] = {r: engines[g].fetch_instance(r, j) for r in ("Reach", "Tri")}
+    for eng in engines:        # the baseline gets the device to itself
+        eng.close()
+    engines = []
     # baseline: one engine call per instance (each rule launched once per instance per round)
     base = pkg.Engine(flags=0)
     pkg.build_program(base, rels, TC_TRI)
-    rng = np.random.default_rng(5)
-    sample = set(rng.choice(instances, min(16, instances), replace=False).tolist())
     base_ms, mism = 0.0, 0
     for i in range(instances):
         for r in rels:
@@ -353,14 +363,10 @@ def batched_measure(instances: int, warmup: int, steps: int) -> dict:
         if base.size("Tri") != sizes_b[i][0] or st["rounds"] != sizes_b[i][1]:
             mism += 1
         if i in sample:
-            g = next(k for k, gg in enumerate(groups) if i in gg)
-            j = groups[g].index(i)
             for r in ("Reach", "Tri"):
-                if not np.array_equal(base.fetch(r), engines[g].fetch_instance(r, j)):
+                if not np.array_equal(base.fetch(r), sample_rows[i][r]):
                     mism += 1
     base.close()
-    for eng in engines:
-        eng.close()
     peak, _ = measured_peak()
     return {"programs_per_s": instances / (ms / 1e3), "ms_per_step": ms, "steps": steps, "warmup": warmup,
             "instances": instances, "groups": len(groups), "edges_total": int(sum(len(e) for e in edges)),
@@ -527,6 +533,53 @@ def run_served_workload(args):
     print(json.dumps(out))
 
 
+def run_points_to_workload(args):
+    """Andersen-style points-to (2M variables, 500k heaps, 2k fields; New 1M, Assign 6M with
+    Zipf(1.1) endpoints, Load / Store 1.5M rows at full scale) at scale 1/pt-scale: the
+    recursive VPT / FPT fixpoint, its rounds, peak device bytes, join slices and the delta
+    kernels' achieved bandwidth."""
+    import torch
+
+    import paper_2604_20073_gb300 as pkg
+    from paper_2604_20073_gb300 import datagen as dg
+    f = 1.0 / args.pt_scale
+    facts = {k: v for k, v in dg.points_to_facts(f, 1002).items() if k != "domains"}
+    stream = torch.cuda.current_stream()
+    eng = pkg.Engine(flags=pkg.DL_FLAG_PROFILE)
+    pkg.build_program(eng, POINTS_TO_RELS, POINTS_TO)
+    for k, v in facts.items():
+        eng.load(k, v)
+    clocks = Clocks(0)
+    times, st = [], None
+    for k in range(args.warmup + args.steps):
+        eng.clear("VPT")
+        eng.clear("FPT")
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = eng.fixpoint()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    peak, _ = measured_peak()
+    kms = {k: v["ms"] for k, v in st["kernels"].items()}
+    kb = {k: v["alg_bytes"] for k, v in st["kernels"].items()}
+    print(json.dumps({"metric": f"fixpoint s (Andersen points-to, facts at scale 1/{args.pt_scale:g})",
+                      "value": ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "higher_is_better": False, "dtype": "u32", "data": "synthetic",
+                      "config": {"workload": "points-to", "scale": f, "seed": 1002,
+                                 "facts": {k: int(len(v)) for k, v in facts.items()}},
+                      "results": {"VPT_rows": eng.size("VPT"), "FPT_rows": eng.size("FPT"), "rounds": st["rounds"],
+                                  "join_rows": int(st["join_rows"]), "delta_rows": int(st["delta_rows"]),
+                                  "peak_bytes": int(st["peak_bytes"]), "join_slices": int(st["join_slices"])},
+                      "kernels": kernel_rates(kms, kb, peak), "gpu_launches": int(st["kernel_launches"]),
+                      "clocks": clk}))
+    eng.close()
+
+
 def run_split_workload(args):
     """Helper-relation splitting ablation (Section 5, CallGraphEdge): the six-atom rule as one
     eight-level join vs split into HelpNT(sn, dsc, h, m) <- HeapAllocationType, MethodLookup
@@ -651,6 +704,8 @@ def main():
         return run_batched_workload(args)
     if args.workload == "served":
         return run_served_workload(args)
+    if args.workload == "points-to":
+        return run_points_to_workload(args)
     import numpy as np
     import torch
 

@@ -101,6 +101,14 @@ typedef struct dl_config {
                                  the remaining levels before the next, so that memory follows
                                  one slice's frontier; 0 = default (a third of the budget left
                                  at that point, at least 64 MiB) */
+    uint32_t head_percent;    /* head/body relations (paper Section 4, Merge): during a recursive
+                                 stratum's rounds each relation is a large body plus a small head
+                                 holding the rows added since the last flush; a round's new rows
+                                 are merged into the head only, and the head is merged into the
+                                 body (one merge-path pass per index, root offsets rebuilt) once
+                                 it exceeds this percentage of the body, and at the stratum's end.
+                                 Joins read body and head as one relation.  0 = default (25),
+                                 UINT32_MAX = flush only at the stratum's end */
     const char* tune_cache;   /* DL_FLAG_AUTOTUNE: text file of tuned choices, read when the
                                  engine is created (if it exists) and rewritten when it is
                                  destroyed or by dl_tune_save; NULL = choices kept in memory */
@@ -114,8 +122,9 @@ typedef struct dl_config {
  * join variable shared by every atom, so instances never join with each other and the
  * work histogram balances uneven instances across the GPU).  Results and per-instance round
  * counts equal those of evaluating each instance alone.  In this form relations have at
- * most DL_MAX_ARITY - 1 columns and rules at most DL_MAX_VARS - 1 variables; count sinks,
- * dl_load_facts*, dl_fetch and dl_fetch_device are not available (DL_ERR_STATE); every
+ * most DL_MAX_ARITY - 1 columns and rules at most DL_MAX_VARS - 1 variables; count sinks
+ * count and digest per instance (dl_instance_digest); dl_load_facts*, dl_fetch and
+ * dl_fetch_device are not available (DL_ERR_STATE); every
  * relation, summed over its instances, holds fewer than 2^32 rows. */
 
 /* ------------------------------------------------------------------ engine */
@@ -310,6 +319,7 @@ typedef struct dl_stats {
                                   (dl_config.frontier_bytes) */
     uint32_t tuned_levels;     /* DL_FLAG_AUTOTUNE: join levels tuned by this call (new buckets) */
     uint32_t tune_hits;        /* DL_FLAG_AUTOTUNE: join levels that used a cached choice */
+    uint32_t head_flushes;     /* heads merged into their bodies (dl_config.head_percent) */
 } dl_stats;
 
 /* Evaluate all rules to the least fixpoint (semi-naive, Jacobi rounds: every rule of a
@@ -342,6 +352,12 @@ int dl_load_facts_instance(dl_engine* e, dl_rel_id rel, uint32_t inst, const uin
  * distinct and sorted as dl_fetch does; NULL cols_out returns only *nrows_out. */
 int dl_fetch_instance(dl_engine* e, dl_rel_id rel, uint32_t inst, uint32_t* const* cols_out, uint64_t cap_rows,
                       uint64_t* nrows_out);
+
+/* Batched form: count and order-independent digest (as dl_fetch_digest defines it, over the
+ * instance's own columns) of one instance's relation; for a count sink, the counts and
+ * digests its rule derived for that instance.  Equals dl_fetch_digest of the instance run
+ * alone.  Errors: DL_ERR_STATE (not a batched engine), DL_ERR_ARG (bad ids). */
+int dl_instance_digest(dl_engine* e, dl_rel_id rel, uint32_t inst, uint64_t* count, uint64_t digest[2]);
 
 /* Batched form, after dl_fixpoint: round count of instance `inst` in each stratum (the
  * count it would have alone, same definition as dl_stats.rounds) into rounds[0..cap);
@@ -468,6 +484,41 @@ int dl_server_result(dl_server* s, uint64_t ticket, dl_engine** engine);
 int dl_server_release(dl_server* s, uint64_t ticket);
 
 int dl_server_get_stats(dl_server* s, dl_server_stats* out);
+
+/* ------------------------------------------------------- batches of programs */
+
+/* Programs evaluated in batches (the paper's problem statement, Section 2, for many
+ * independent programs at once).  A dl_program describes relations, rules and host facts of
+ * one program without touching the device; dl_fixpoint_batch evaluates many programs:
+ * programs of the same shape (equal relations, sinks and rules; facts may differ) form a group
+ * that runs in the batched form of the engine (see dl_config.instances), so each evaluation
+ * stage of a group is one launch over all of its programs; groups run one after another on
+ * the engine's stream, with the engine's configuration.  Results and round counts equal
+ * those of each program run alone.  A group's results stay in device memory (taken from the
+ * engine's budget left when the batch ran) until its last program is destroyed.
+ * Relations have at most DL_MAX_ARITY - 1 columns and rules at most DL_MAX_VARS - 1
+ * variables.  The rule and relation calls have the semantics of dl_relation_create,
+ * dl_relation_set_sink and dl_rule_add_ex; they are checked when the batch runs. */
+typedef struct dl_program dl_program;
+int dl_program_create(dl_engine* e, dl_program** out);
+void dl_program_destroy(dl_program* p);
+const char* dl_program_last_error(const dl_program* p);
+int dl_program_relation(dl_program* p, const char* name, uint32_t arity, uint32_t sink, dl_rel_id* out);
+int dl_program_rule(dl_program* p, const dl_atom* head, const dl_atom* body, uint32_t nbody, const dl_atom* neg,
+                    uint32_t nneg, const dl_cmp* cmps, uint32_t ncmp, const uint32_t* var_order, uint32_t nvars);
+/* Host facts, copied (cols[j] points to nrows values of column j). */
+int dl_program_load_facts(dl_program* p, dl_rel_id rel, const uint32_t* const* cols, uint64_t nrows);
+/* Evaluate n programs (all created on e); per_prog (NULL or n entries) receives each program's
+ * group's statistics.  Errors: the first failing group's status (its programs keep the text in
+ * dl_program_last_error and no result); DL_ERR_ARG (a program of another engine). */
+int dl_fixpoint_batch(dl_engine* e, dl_program* const* progs, uint32_t n, dl_stats* per_prog);
+/* Results of an evaluated program: rows (as dl_fetch: two-call pattern, sorted columns to
+ * HOST buffers), digest (as dl_fetch_digest; count sinks too), rounds per stratum and the
+ * relations of each stratum.  DL_ERR_STATE before the program has been evaluated. */
+int dl_program_fetch(dl_program* p, dl_rel_id rel, uint32_t* const* cols_out, uint64_t cap_rows, uint64_t* nrows_out);
+int dl_program_digest(dl_program* p, dl_rel_id rel, uint64_t* count, uint64_t digest[2]);
+int dl_program_rounds(dl_program* p, uint32_t* rounds, uint32_t cap, uint32_t* nstrata);
+int dl_program_stratum(dl_program* p, uint32_t s, dl_rel_id* rels, uint32_t cap, uint32_t* nrels);
 
 /* Write the autotuner's choices (DL_FLAG_AUTOTUNE) to a text file, one per line: the key
  * (rule shape hash, level, log2 of units and entries, sources, filters), the tile size, the

@@ -50,7 +50,7 @@ class dl_config(ctypes.Structure):
                 ("alloc", DL_ALLOC_FN), ("free", DL_FREE_FN), ("alloc_user", ctypes.c_void_p),
                 ("flags", ctypes.c_uint32), ("tile_units", ctypes.c_uint32), ("instances", ctypes.c_uint32),
                 ("chunk_rows", ctypes.c_uint64), ("hub_rows", ctypes.c_uint32),
-                ("frontier_bytes", ctypes.c_uint64), ("tune_cache", ctypes.c_char_p)]
+                ("frontier_bytes", ctypes.c_uint64), ("head_percent", ctypes.c_uint32), ("tune_cache", ctypes.c_char_p)]
 
 
 class dl_term(ctypes.Structure):
@@ -79,7 +79,8 @@ class dl_stats(ctypes.Structure):
                 ("ms_dedup", ctypes.c_double), ("ms_merge", ctypes.c_double),
                 ("kernels", dl_kernel_stat * len(KERNEL_KINDS)), ("top_kind", ctypes.c_uint32),
                 ("top", dl_kernel_stat), ("hub_keys", ctypes.c_uint32),
-                ("join_slices", ctypes.c_uint32), ("tuned_levels", ctypes.c_uint32), ("tune_hits", ctypes.c_uint32)]
+                ("join_slices", ctypes.c_uint32), ("tuned_levels", ctypes.c_uint32), ("tune_hits", ctypes.c_uint32),
+                ("head_flushes", ctypes.c_uint32)]
 
 
 class dl_server_config(ctypes.Structure):
@@ -151,6 +152,7 @@ _SIGS = {
     "dl_fetch_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_u32p),
                                          ctypes.c_uint64, _u64p]),
     "dl_instance_rounds": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p]),
+    "dl_instance_digest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p]),
     "dl_server_create": (ctypes.c_int, [ctypes.POINTER(dl_server_config), ctypes.POINTER(ctypes.c_void_p)]),
     "dl_server_destroy": (None, [ctypes.c_void_p]),
     "dl_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_request), _u64p]),
@@ -161,6 +163,20 @@ _SIGS = {
     "dl_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "dl_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_server_stats)]),
     "dl_tune_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "dl_program_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "dl_program_destroy": (None, [ctypes.c_void_p]),
+    "dl_program_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "dl_program_relation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_uint32, ctypes.c_uint32, _u32p]),
+    "dl_program_rule": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_atom), ctypes.POINTER(dl_atom), ctypes.c_uint32,
+                                       ctypes.POINTER(dl_atom), ctypes.c_uint32, ctypes.POINTER(dl_cmp), ctypes.c_uint32,
+                                       _u32p, ctypes.c_uint32]),
+    "dl_program_load_facts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(_u32p), ctypes.c_uint64]),
+    "dl_fixpoint_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
+                                         ctypes.POINTER(dl_stats)]),
+    "dl_program_fetch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(_u32p), ctypes.c_uint64, _u64p]),
+    "dl_program_digest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p]),
+    "dl_program_rounds": (ctypes.c_int, [ctypes.c_void_p, _u32p, ctypes.c_uint32, _u32p]),
+    "dl_program_stratum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u32p, ctypes.c_uint32, _u32p]),
     "dl_sort_unique_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32, ctypes.c_uint64,
                                               ctypes.POINTER(ctypes.c_void_p), _u64p, ctypes.c_void_p]),
 }
@@ -206,12 +222,56 @@ def _cols_ptrs(arrs):
     return arr
 
 
+def _encode_atom(rel_ids, atom, var_ids, keep):
+    rel, terms = atom
+    ts = (dl_term * len(terms))()
+    for i, t in enumerate(terms):
+        if isinstance(t, str):
+            ts[i].kind, ts[i].id = DL_TERM_VAR, var_ids.setdefault(t, len(var_ids))
+        else:
+            ts[i].kind, ts[i].id = DL_TERM_CONST, int(t)
+    keep.append(ts)
+    a = dl_atom()
+    a.rel, a.arity, a.terms = rel_ids[rel], len(terms), ts
+    return a
+
+
+def _encode_rule(rel_ids, head, body, order):
+    """ctypes arguments of a rule: body items are atoms (rel, [terms]), negated atoms
+    ("not", atom) and comparisons (op, term, term) with op in < <= > >= !=."""
+    var_ids: dict = {}
+    keep: list = []
+    pos = [b for b in body if len(b) == 2 and b[0] != "not"]
+    neg = [b[1] for b in body if len(b) == 2 and b[0] == "not"]
+    cmps = [b for b in body if len(b) == 3]
+    batoms = (dl_atom * len(pos))()
+    for i, b in enumerate(pos):
+        batoms[i] = _encode_atom(rel_ids, b, var_ids, keep)
+    natoms = (dl_atom * max(1, len(neg)))()
+    for i, b in enumerate(neg):
+        natoms[i] = _encode_atom(rel_ids, b, var_ids, keep)
+    carr = (dl_cmp * max(1, len(cmps)))()
+    for i, (op, a, b) in enumerate(cmps):
+        if op in (">", ">="):
+            op, a, b = ("<" if op == ">" else "<="), b, a
+        carr[i].op = {"<": DL_CMP_LT, "<=": DL_CMP_LE, "!=": DL_CMP_NE}[op]
+        for t, dst in ((a, carr[i].a), (b, carr[i].b)):
+            if isinstance(t, str):
+                dst.kind, dst.id = DL_TERM_VAR, var_ids.get(t, 1023)
+            else:
+                dst.kind, dst.id = DL_TERM_CONST, int(t)
+    h = _encode_atom(rel_ids, head, var_ids, keep)
+    ordr = (ctypes.c_uint32 * len(order))(*[var_ids.get(v, 1023) for v in order])
+    keep += [batoms, natoms, carr, ordr]
+    return h, batoms, len(pos), natoms, len(neg), carr, len(cmps), ordr, len(order), keep
+
+
 class Engine:
     """One engine handle (owns all of its device memory)."""
 
     def __init__(self, device: int = 0, stream=None, arena_bytes: int = 0, flags: int = 0, tile_units: int = 0,
                  use_torch_allocator: bool = False, instances: int = 0, chunk_rows: int = 0, hub_rows: int = 0,
-                 frontier_bytes: int = 0, tune_cache: str | None = None):
+                 frontier_bytes: int = 0, tune_cache: str | None = None, head_percent: int = 0):
         import torch  # plumbing only: stream handle and (optionally) the caching allocator
         self.lib = load_library()
         if not torch.cuda.is_available():
@@ -230,6 +290,7 @@ class Engine:
         cfg.chunk_rows = chunk_rows
         cfg.hub_rows = hub_rows
         cfg.frontier_bytes = frontier_bytes
+        cfg.head_percent = head_percent
         self._tune_cache = tune_cache.encode() if tune_cache else None   # kept alive for the engine
         cfg.tune_cache = self._tune_cache
         self.instances = instances
@@ -318,6 +379,13 @@ class Engine:
         self._check(self.lib.dl_fetch_instance(self.h, rid, inst, _cols_ptrs(cols), n.value, ctypes.byref(n)))
         return np.stack(cols, axis=1)
 
+    def instance_digest(self, name: str, inst: int) -> tuple:
+        """Batched form: (count, sum, xor) digest of one instance's relation (count sinks too)."""
+        c = ctypes.c_uint64()
+        d = (ctypes.c_uint64 * 2)()
+        self._check(self.lib.dl_instance_digest(self.h, self.rel_ids[name], inst, ctypes.byref(c), d))
+        return (c.value, d[0], d[1])
+
     def instance_rounds(self, inst: int) -> list:
         r = (ctypes.c_uint32 * DL_MAX_STRATA)()
         ns = ctypes.c_uint32()
@@ -328,51 +396,18 @@ class Engine:
         self._check(self.lib.dl_relation_clear(self.h, self.rel_ids[name]))
 
     def _atom(self, atom, var_ids, keep):
-        rel, terms = atom
-        ts = (dl_term * len(terms))()
-        for i, t in enumerate(terms):
-            if isinstance(t, str):
-                ts[i].kind, ts[i].id = DL_TERM_VAR, var_ids.setdefault(t, len(var_ids))
-            else:
-                ts[i].kind, ts[i].id = DL_TERM_CONST, int(t)
-        keep.append(ts)
-        a = dl_atom()
-        a.rel, a.arity, a.terms = self.rel_ids[rel], len(terms), ts
-        return a
+        return _encode_atom(self.rel_ids, atom, var_ids, keep)
 
     def rule(self, head, body, order):
         """Add a rule.  body items: atoms (rel, [terms]), negated atoms ("not", atom) and
         comparisons (op, term, term) with op in < <= > >= != (dl_rule_add_ex)."""
-        var_ids: dict = {}
-        keep: list = []
-        pos = [b for b in body if len(b) == 2 and b[0] != "not"]
-        neg = [b[1] for b in body if len(b) == 2 and b[0] == "not"]
-        cmps = [b for b in body if len(b) == 3]
-        batoms = (dl_atom * len(pos))()
-        for i, b in enumerate(pos):
-            batoms[i] = self._atom(b, var_ids, keep)
-        natoms = (dl_atom * max(1, len(neg)))()
-        for i, b in enumerate(neg):
-            natoms[i] = self._atom(b, var_ids, keep)
-        carr = (dl_cmp * max(1, len(cmps)))()
-        for i, (op, a, b) in enumerate(cmps):
-            if op in (">", ">="):
-                op, a, b = ("<" if op == ">" else "<="), b, a
-            carr[i].op = {"<": DL_CMP_LT, "<=": DL_CMP_LE, "!=": DL_CMP_NE}[op]
-            for t, dst in ((a, carr[i].a), (b, carr[i].b)):
-                if isinstance(t, str):
-                    dst.kind, dst.id = DL_TERM_VAR, var_ids.get(t, 1023)
-                else:
-                    dst.kind, dst.id = DL_TERM_CONST, int(t)
-        h = self._atom(head, var_ids, keep)
-        ordr = (ctypes.c_uint32 * len(order))(*[var_ids.get(v, 1023) for v in order])
+        h, batoms, npos, natoms, nneg, carr, ncmp, ordr, norder, keep = _encode_rule(self.rel_ids, head, body, order)
         rid = ctypes.c_uint32()
-        if neg or cmps:
-            self._check(self.lib.dl_rule_add_ex(self.h, ctypes.byref(h), batoms, len(pos), natoms, len(neg), carr,
-                                                len(cmps), ordr, len(order), ctypes.byref(rid)))
+        if nneg or ncmp:
+            self._check(self.lib.dl_rule_add_ex(self.h, ctypes.byref(h), batoms, npos, natoms, nneg, carr, ncmp, ordr,
+                                                norder, ctypes.byref(rid)))
         else:
-            self._check(self.lib.dl_rule_add(self.h, ctypes.byref(h), batoms, len(pos), ordr, len(order),
-                                             ctypes.byref(rid)))
+            self._check(self.lib.dl_rule_add(self.h, ctypes.byref(h), batoms, npos, ordr, norder, ctypes.byref(rid)))
         return rid.value
 
     def rule_split(self, head, body, order, factored, helper: str):
@@ -627,6 +662,94 @@ def split_columns(head, body, order, factored) -> list:
     return [names[c] for c in cols[: k.value]]
 
 
+class Program:
+    """A program for dl_fixpoint_batch (dl_program_*): relations, rules and host facts; after
+    fixpoint_batch its results are read with fetch / digest / strata."""
+
+    def __init__(self, engine: Engine, relations: dict, rules: list, sinks: dict | None = None):
+        self.lib = engine.lib
+        self.engine = engine
+        h = ctypes.c_void_p()
+        rc = self.lib.dl_program_create(engine.h, ctypes.byref(h))
+        if rc != DL_OK:
+            raise DatalogError(rc, "dl_program_create failed")
+        self.h = h
+        self.rel_ids, self.arity, self.names = {}, {}, list(relations)
+        for name, a in relations.items():
+            rid = ctypes.c_uint32()
+            self._check(self.lib.dl_program_relation(self.h, name.encode(), a, (sinks or {}).get(name, DL_SINK_STORE),
+                                                     ctypes.byref(rid)))
+            self.rel_ids[name] = rid.value
+            self.arity[name] = a
+        self.sinks = dict(sinks or {})
+        for r in rules:
+            h_, batoms, npos, natoms, nneg, carr, ncmp, ordr, norder, keep = _encode_rule(self.rel_ids, r[0], r[1], r[2])
+            self._check(self.lib.dl_program_rule(self.h, ctypes.byref(h_), batoms, npos, natoms, nneg, carr, ncmp, ordr,
+                                                 norder))
+
+    def _check(self, rc):
+        if rc != DL_OK:
+            raise DatalogError(rc, self.lib.dl_program_last_error(self.h).decode())
+
+    def load(self, name: str, rows):
+        rows = np.asarray(rows, dtype=np.uint32).reshape(-1, self.arity[name])
+        cols = [np.ascontiguousarray(rows[:, c]) for c in range(rows.shape[1])]
+        self._check(self.lib.dl_program_load_facts(self.h, self.rel_ids[name], _cols_ptrs(cols), rows.shape[0]))
+
+    def fetch(self, name: str) -> np.ndarray:
+        n = ctypes.c_uint64()
+        rid = self.rel_ids[name]
+        self._check(self.lib.dl_program_fetch(self.h, rid, None, 0, ctypes.byref(n)))
+        cols = [np.empty(n.value, dtype=np.uint32) for _ in range(self.arity[name])]
+        self._check(self.lib.dl_program_fetch(self.h, rid, _cols_ptrs(cols), n.value, ctypes.byref(n)))
+        return np.stack(cols, axis=1)
+
+    def digest(self, name: str) -> tuple:
+        c = ctypes.c_uint64()
+        d = (ctypes.c_uint64 * 2)()
+        self._check(self.lib.dl_program_digest(self.h, self.rel_ids[name], ctypes.byref(c), d))
+        return (c.value, d[0], d[1])
+
+    def strata(self) -> list:
+        r = (ctypes.c_uint32 * DL_MAX_STRATA)()
+        ns = ctypes.c_uint32()
+        self._check(self.lib.dl_program_rounds(self.h, r, DL_MAX_STRATA, ctypes.byref(ns)))
+        out = []
+        for s in range(ns.value):
+            rels = (ctypes.c_uint32 * 256)()
+            n = ctypes.c_uint32()
+            self._check(self.lib.dl_program_stratum(self.h, s, rels, 256, ctypes.byref(n)))
+            out.append((sorted(self.names[i] for i in rels[: n.value]), r[s]))
+        return out
+
+    def result(self) -> dict:
+        return {name: (self.digest(name) if self.sinks.get(name) == DL_SINK_COUNT else self.fetch(name))
+                for name in self.names}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dl_program_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fixpoint_batch(engine: Engine, programs: list) -> list:
+    """Evaluate programs together (dl_fixpoint_batch); returns each program's group stats."""
+    arr = (ctypes.c_void_p * len(programs))(*[p.h.value for p in programs])
+    st = (dl_stats * len(programs))()
+    rc = engine.lib.dl_fixpoint_batch(engine.h, arr, len(programs), st)
+    if rc != DL_OK:
+        msgs = [p.lib.dl_program_last_error(p.h).decode() for p in programs]
+        raise DatalogError(rc, "dl_fixpoint_batch failed: " + next((m for m in msgs if m), ""))
+    return [{"rounds": list(s.rounds[: min(s.nstrata, DL_MAX_STRATA)]), "kernel_launches": s.kernel_launches,
+             "peak_bytes": s.peak_bytes} for s in st]
+
+
 def build_program(eng: Engine, relations: dict, rules: list, sinks: dict | None = None):
     for name, a in relations.items():
         eng.relation(name, a)
@@ -636,12 +759,13 @@ def build_program(eng: Engine, relations: dict, rules: list, sinks: dict | None 
         eng.rule(r[0], r[1], r[2])
 
 
-def run_batched(relations: dict, facts_per_instance: list, rules: list, **cfg):
+def run_batched(relations: dict, facts_per_instance: list, rules: list, sinks: dict | None = None, **cfg):
     """Evaluate independent instances of one program together (batched form); returns
-    (per-instance relations dicts, per-instance [(stratum relation names, rounds)], stats)."""
+    (per-instance relations dicts, per-instance [(stratum relation names, rounds)], stats).
+    Count sinks give their per-instance (count, sum, xor) digest instead of rows."""
     n = len(facts_per_instance)
     with Engine(instances=n, **cfg) as eng:
-        build_program(eng, relations, rules)
+        build_program(eng, relations, rules, sinks)
         for i, facts in enumerate(facts_per_instance):
             for name, rows in facts.items():
                 if len(rows):
@@ -650,7 +774,8 @@ def run_batched(relations: dict, facts_per_instance: list, rules: list, **cfg):
         strata = eng.strata()
         outs, rounds = [], []
         for i in range(n):
-            outs.append({name: eng.fetch_instance(name, i) for name in relations})
+            outs.append({name: (eng.instance_digest(name, i) if (sinks or {}).get(name) == DL_SINK_COUNT
+                                else eng.fetch_instance(name, i)) for name in relations})
             r = eng.instance_rounds(i)
             rounds.append([(rels, r[k]) for k, (rels, _) in enumerate(strata)])
         return outs, rounds, stats

@@ -476,6 +476,8 @@ struct PendingOut {
     uint32_t producers = 0;   // variants that produced parts
 };
 
+void run_variant_on(Engine& E, const Variant& v, std::vector<const Index*>& src, std::map<uint32_t, PendingOut>& outs);
+
 // Drop the rows of a raw (unsorted) table that are already in full, before any sorting: in
 // late rounds most join output rediscovers known tuples, so the sort then only sees rows
 // that may be new.  The join emits rows grouped by their leading columns, so consecutive
@@ -483,16 +485,47 @@ struct PendingOut {
 // The result's columns lie t.n (the unfiltered count) values apart: see `stride`.
 std::pair<DevPtr, TableView> prefilter(Engine& E, const Relation& R, DevPtr buf, TableView t, uint64_t& stride) {
     stride = t.n;
-    if (R.full[0].n == 0 || t.n == 0) return {buf, t};
-    DevPtr out = E.make(sizeof(uint32_t) * t.arity * t.n);
-    TableView o;
-    memset(&o, 0, sizeof(o));
-    o.arity = t.arity;
-    for (uint32_t c = 0; c < t.arity; c++) o.col[c] = (uint32_t*)out->ptr + (size_t)c * t.n;
+    // the relation is its body and, during recursive rounds, its head
+    for (const Index* part : {&R.full[0], R.head.empty() ? nullptr : &R.head[0]}) {
+        if (!part || part->n == 0 || t.n == 0) continue;
+        DevPtr out = E.make(sizeof(uint32_t) * t.arity * stride);
+        TableView o;
+        memset(&o, 0, sizeof(o));
+        o.arity = t.arity;
+        for (uint32_t c = 0; c < t.arity; c++) o.col[c] = (uint32_t*)out->ptr + (size_t)c * stride;
+        E.phase_begin(2);
+        o.n = anti_filter(E, t, atom_of(*part), o, false);   // sorted next: order does not matter
+        E.phase_end(2);
+        buf = out;
+        t = o;
+    }
+    return {buf, t};
+}
+
+// Rows of a sorted index absent from the relation's head (order kept).
+Index minus_head(Engine& E, const Relation& R, const Index& d) {
+    if (R.head.empty() || R.head[0].n == 0 || d.n == 0) return d;
+    Perm p = identity_perm();
+    for (int k = 0; k < kMaxArity; k++) p[k] = d.perm[k];
+    Index o = make_index(E, d.arity, p, d.n);
     E.phase_begin(2);
-    o.n = anti_filter(E, t, atom_of(R.full[0]), o);
+    o.n = anti_filter(E, table_of(d), atom_of(R.head[0]), table_of(o));
     E.phase_end(2);
-    return {out, o};
+    return o;
+}
+
+// Head/body: merge every head into its body and rebuild the body's root offsets.
+void flush_head(Engine& E, Relation& R) {
+    if (R.head.empty()) return;
+    if (R.head[0].n) {
+        for (size_t k = 0; k < R.perms.size(); k++) {
+            R.full[k] = merge_into(E, R.full[k], R.head[k]);
+            build_roots(E, R.full[k], R.root_needed[k]);
+        }
+        check_sorted(E, R.full[0], R.name);
+        E.head_flushes++;
+    }
+    for (size_t k = 0; k < R.head.size(); k++) R.head[k] = empty_index(R.arity, R.perms[k]);
 }
 
 // a ∪ b of two sorted, duplicate-free indexes (rows may occur in both).
@@ -568,9 +601,11 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
         newrows = sort_into_index(E, f.first, f.second, identity_perm(), R.arity, stride);
         filtered = true;
     }
-    if (!d.cols && d.n == 0)
+    if (!d.cols && d.n == 0) {
         d = compute_delta(E, newrows, filtered ? empty_index(R.arity, identity_perm()) : R.full[0], identity_perm(),
                           R.arity, known_unique);
+        if (!filtered) d = minus_head(E, R, d);
+    }
     jo.parts.clear();
     jo.owners.clear();
     E.delta_rows += d.n;
@@ -579,18 +614,34 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
         R.delta[0] = d;
     }
     if (d.n == 0) return 0;
-    R.full[0] = merge_into(E, R.full[0], d);
-    check_sorted(E, R.full[0], R.name);
-    build_roots(E, R.full[0], R.root_needed[0]);
+    // Recursive rounds (head/body form): Δ is merged into the small head; the body, and its
+    // root offsets, stay as they are until the head outgrows E.head_percent of it (paper
+    // Section 4, Merge: new tuples go to the head, which is flushed into the body by one
+    // merge-path pass above a threshold).  Round 1 merges straight into full.
+    const bool to_head = keep_delta && !R.head.empty();
+    if (to_head) {
+        R.head[0] = merge_into(E, R.head[0], d);
+        check_sorted(E, R.head[0], R.name);
+    } else {
+        R.full[0] = merge_into(E, R.full[0], d);
+        check_sorted(E, R.full[0], R.name);
+        build_roots(E, R.full[0], R.root_needed[0]);
+    }
     for (size_t k = 1; k < R.perms.size(); k++) {
         Index dk = permuted_sorted(E, d, R.perms[k]);
-        R.full[k] = merge_into(E, R.full[k], dk);
-        build_roots(E, R.full[k], R.root_needed[k]);
+        if (to_head) {
+            R.head[k] = merge_into(E, R.head[k], dk);
+        } else {
+            R.full[k] = merge_into(E, R.full[k], dk);
+            build_roots(E, R.full[k], R.root_needed[k]);
+        }
         if (keep_delta) {
             build_roots(E, dk, R.root_needed[k]);
             R.delta[k] = dk;
         }
     }
+    if (to_head && E.head_percent != UINT32_MAX && R.head[0].n * 100 > (uint64_t)E.head_percent * R.full[0].n)
+        flush_head(E, R);
     if (keep_delta) {
         Index d0 = d;
         build_roots(E, d0, R.root_needed[0]);
@@ -603,11 +654,27 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
 void run_variant(Engine& E, const Variant& v, std::map<uint32_t, PendingOut>& outs) {
     const Rule& r = *v.rule;
     std::vector<const Index*> src(r.body.size());
+    std::vector<std::pair<size_t, const Index*>> heads;   // atoms reading a relation in head/body form
     for (size_t a = 0; a < r.body.size(); a++) {
         Relation& B = E.rels[r.body[a].rel];
         uint32_t slot = perm_slot(B, atom_perm(r, (uint32_t)a));
         src[a] = (int)a == v.delta_atom ? &B.delta[slot] : &B.full[slot];
+        if ((int)a != v.delta_atom && slot < B.head.size() && B.head[slot].n) heads.push_back({a, &B.head[slot]});
     }
+    if (heads.size() > 16) throw Error(DL_ERR_UNSUPPORTED, "more than 16 atoms read relations in head/body form");
+    // full = body ∪ head (disjoint): the variant is the union of its evaluations with each such
+    // atom reading either part
+    const std::vector<const Index*> bodies = src;
+    for (uint32_t m = 0; m < (1u << heads.size()); m++) {
+        src = bodies;
+        for (size_t h = 0; h < heads.size(); h++)
+            if ((m >> h) & 1u) src[heads[h].first] = heads[h].second;
+        run_variant_on(E, v, src, outs);
+    }
+}
+
+void run_variant_on(Engine& E, const Variant& v, std::vector<const Index*>& src, std::map<uint32_t, PendingOut>& outs) {
+    const Rule& r = *v.rule;
     std::vector<const Index*> nsrc(r.neg.size());   // negated relations: lower strata, read in full
     for (size_t a = 0; a < r.neg.size(); a++) {
         Relation& B = E.rels[r.neg[a].rel];
@@ -617,9 +684,14 @@ void run_variant(Engine& E, const Variant& v, std::map<uint32_t, PendingOut>& ou
     PendingOut& po = outs[r.head.rel];
     JoinOutput jo;
     if (H.sink != DL_SINK_COUNT)
+        // each chunk is reduced (rows already in the relation dropped, sorted, deduplicated) and
+        // folded into one accumulated part at once, so memory follows the new rows, not the
+        // raw bindings of all chunks
         jo.chunk_sink = [&E, &H, &jo](DevPtr buf, TableView t) {
             Index rp = reduce_part(E, H, buf, t);
-            if (rp.n) jo.rparts.push_back(rp);
+            if (!rp.n) return;
+            if (jo.rparts.empty()) jo.rparts.push_back(rp);
+            else jo.rparts[0] = union_sorted(E, jo.rparts[0], rp);
         };
     run_join(E, r, src, nsrc, H, jo);
     if (!jo.parts.empty() || !jo.rparts.empty()) {
@@ -658,7 +730,7 @@ void fixpoint(Engine& E, dl_stats* st) {
     auto t0 = std::chrono::steady_clock::now();
     const uint64_t launches0 = E.launches;
     const uint64_t hub0 = E.hub_keys, slices0 = E.join_slices;
-    const uint64_t tuned0 = E.tuned_levels, hits0 = E.tune_hits;
+    const uint64_t tuned0 = E.tuned_levels, hits0 = E.tune_hits, flush0 = E.head_flushes;
     E.join_rows = E.count_rows = E.delta_rows = 0;
     E.peak = E.used;
     E.event_next = 0;
@@ -684,6 +756,7 @@ void fixpoint(Engine& E, dl_stats* st) {
         if (R.sink == DL_SINK_COUNT) {
             R.sink_count = 0;
             R.sink_digest[0] = R.sink_digest[1] = 0;
+            R.sink_inst.assign(3ull * E.instances, 0);
             continue;
         }
         ensure_full_perms(E, R);
@@ -734,18 +807,42 @@ void fixpoint(Engine& E, dl_stats* st) {
         }
         uint32_t t = 1;
         if (!rec.empty() && any) {
-            for (;;) {
-                t++;
-                outs.clear();
-                for (const Variant& v : rec) run_variant(E, v, outs);
-                uint64_t nd = 0;
-                for (uint32_t r : S.rels) {
-                    Relation& R = E.rels[r];
-                    if (R.sink == DL_SINK_COUNT) continue;
-                    nd += absorb_round(E, R, outs[r], true);
-                    if (E.instances) mark_runs(E, R.delta[0].col(0), R.delta[0].n, last.p, t);
+            // the stratum's relations take the head/body form for the rounds
+            for (uint32_t r : S.rels) {
+                Relation& R = E.rels[r];
+                if (R.sink == DL_SINK_COUNT) continue;
+                R.head.clear();
+                for (size_t k = 0; k < R.perms.size(); k++) R.head.push_back(empty_index(R.arity, R.perms[k]));
+            }
+            try {
+                for (;;) {
+                    t++;
+                    outs.clear();
+                    for (const Variant& v : rec) run_variant(E, v, outs);
+                    uint64_t nd = 0;
+                    for (uint32_t r : S.rels) {
+                        Relation& R = E.rels[r];
+                        if (R.sink == DL_SINK_COUNT) continue;
+                        nd += absorb_round(E, R, outs[r], true);
+                        if (E.instances) mark_runs(E, R.delta[0].col(0), R.delta[0].n, last.p, t);
+                    }
+                    if (nd == 0) break;
                 }
-                if (nd == 0) break;
+            } catch (...) {
+                // keep the completed rounds: merge what the heads hold back into the bodies
+                outs.clear();
+                for (uint32_t r : S.rels) {
+                    try {
+                        flush_head(E, E.rels[r]);
+                    } catch (...) {
+                    }
+                    E.rels[r].head.clear();
+                }
+                throw;
+            }
+            for (uint32_t r : S.rels) {
+                flush_head(E, E.rels[r]);
+                E.rels[r].head.clear();
             }
         }
         S.rounds = t;
@@ -784,6 +881,7 @@ void fixpoint(Engine& E, dl_stats* st) {
         st->join_slices = (uint32_t)(E.join_slices - slices0);
         st->tuned_levels = (uint32_t)(E.tuned_levels - tuned0);
         st->tune_hits = (uint32_t)(E.tune_hits - hits0);
+        st->head_flushes = (uint32_t)(E.head_flushes - flush0);
         double* ms[4] = {&st->ms_join, &st->ms_sort, &st->ms_dedup, &st->ms_merge};
         for (int k = 0; k < 4; k++)
             for (auto& pr : E.phases.ev[k]) {
@@ -889,6 +987,7 @@ int dl_engine_create(const dl_config* cfg, dl_engine** out) {
         E->instances = c.instances;
         if (c.chunk_rows) E->chunk_rows = c.chunk_rows;
         if (c.hub_rows) E->hub_rows = c.hub_rows;
+        if (c.head_percent) E->head_percent = c.head_percent;
         E->frontier_bytes = c.frontier_bytes;
         if (c.tune_cache) {
             E->tune_path = c.tune_cache;
@@ -951,7 +1050,6 @@ int dl_relation_set_sink(dl_engine* e, dl_rel_id rel, uint32_t sink) {
         if (sink != DL_SINK_STORE && sink != DL_SINK_COUNT) throw Error(DL_ERR_ARG, "bad sink");
         if (sink == DL_SINK_COUNT && (R.full[0].n || !R.pending.empty()))
             throw Error(DL_ERR_STATE, "relation already holds tuples");
-        if (sink == DL_SINK_COUNT && E.instances) throw Error(DL_ERR_STATE, "count sinks are not available on a batched engine");
         R.sink = sink;
     });
 }
@@ -1031,6 +1129,7 @@ int dl_relation_clear(dl_engine* e, dl_rel_id rel) {
         R.full_perms_built = true;
         R.sink_count = 0;
         R.sink_digest[0] = R.sink_digest[1] = 0;
+        R.sink_inst.assign(3ull * E.instances, 0);
     });
 }
 
@@ -1376,6 +1475,39 @@ int dl_fetch_instance(dl_engine* e, dl_rel_id rel, uint32_t inst, uint32_t* cons
                                         cudaMemcpyDeviceToHost, E.stream));
         }
         E.sync();
+    });
+}
+
+int dl_instance_digest(dl_engine* e, dl_rel_id rel, uint32_t inst, uint64_t* count, uint64_t digest[2]) {
+    return guard(e, [&](Engine& E) {
+        if (!E.instances) throw Error(DL_ERR_STATE, "dl_instance_digest needs a batched engine");
+        Relation& R = rel_of(E, rel);
+        if (inst >= E.instances) throw Error(DL_ERR_ARG, "instance out of range");
+        if (!count || !digest) throw Error(DL_ERR_ARG, "null output");
+        if (R.sink == DL_SINK_COUNT) {
+            const bool have = R.sink_inst.size() == 3ull * E.instances;
+            *count = have ? R.sink_inst[3ull * inst] : 0;
+            digest[0] = have ? R.sink_inst[3ull * inst + 1] : 0;
+            digest[1] = have ? R.sink_inst[3ull * inst + 2] : 0;
+            return;
+        }
+        flush_pending(E, R);
+        const Index& ix = R.full[0];
+        uint64_t lo = 0, hi = 0;
+        find_range(E, ix.col(0), ix.n, inst, &lo, &hi);
+        // the instance's rows without the instance column: the digest of the instance alone
+        TableView t;
+        memset(&t, 0, sizeof(t));
+        t.arity = R.user_arity;
+        t.n = hi - lo;
+        for (uint32_t c = 0; c < R.user_arity; c++) t.col[c] = ix.col((int)c + 1) + lo;
+        auto d = E.array<uint64_t>(3);
+        DL_CUDA(cudaMemsetAsync(d.p, 0, 24, E.stream));
+        table_digest(E, t, (unsigned long long*)d.p);
+        const uint64_t* h = E.readback(d.p, 3);
+        *count = h[0];
+        digest[0] = h[1];
+        digest[1] = h[2];
     });
 }
 

@@ -169,7 +169,8 @@ void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev, bool i
 
 // Sort the rows of t (arity columns, n rows) lexicographically, col[0] most significant.
 // tmp must have the same shape; on return t holds the sorted rows (buffers may be swapped).
-void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out);
+// allow_pack: rows whose varying bits fit in 64 bits are sorted as packed keys.
+void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out, bool allow_pack = true);
 
 // Keep rows that differ from their predecessor and (if full.n > 0) are absent from full.
 // in is sorted; writes the kept rows, in order, to out; returns the count (synchronises).
@@ -177,7 +178,8 @@ uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const
 
 // Keep the rows of in (any order) that are absent from full; order is kept; returns the
 // count (synchronises).
-uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const TableView& out);
+// keep_order = false: one pass, rows come out in no particular order.
+uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const TableView& out, bool keep_order = true);
 
 // out = merge(a, b) of two sorted, disjoint tables (a.n + b.n rows).
 void merge_rows(Engine& E, const TableView& a, const TableView& b, const TableView& out);

@@ -28,10 +28,15 @@ struct Relation {
     std::vector<Perm> perms;          // perms[0] is the identity (canonical order)
     std::vector<Index> full;          // one index per perm; full[0] is always valid
     std::vector<Index> delta;         // one index per perm (valid during a stratum's rounds)
+    // Head/body form during a recursive stratum's rounds: full[k] is the body and head[k] the
+    // rows added since the last flush; the relation is their (disjoint) union.  Empty outside
+    // the rounds: the stratum's end flushes every head into its body.
+    std::vector<Index> head;
     bool full_perms_built = false;    // full[k > 0] are up to date
     std::vector<bool> root_needed;    // per perm: build dense root offsets
     uint64_t sink_count = 0;
     unsigned long long sink_digest[2] = {0, 0};
+    std::vector<uint64_t> sink_inst;  // batched count sink: per instance [count, sum, xor]
     int stratum = -1;
 };
 
@@ -105,6 +110,8 @@ class Engine {
     uint64_t join_rows = 0, count_rows = 0, delta_rows = 0;
     uint64_t frontier_bytes = 0;      // join frontier bytes before slicing (0: a third of the budget left)
     uint64_t join_slices = 0;         // levels whose input was processed in slices
+    uint32_t head_percent = 25;       // flush a head into its body above this percentage of the body
+    uint64_t head_flushes = 0;
     std::map<std::string, TuneChoice> tune;   // DL_FLAG_AUTOTUNE: choices by rule, level and size bucket
     std::string tune_path;            // file the choices are loaded from and saved to ("" = none)
     uint64_t tuned_levels = 0, tune_hits = 0;

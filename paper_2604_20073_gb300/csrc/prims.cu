@@ -7,6 +7,7 @@
 // (single-pass GPU merge path, Green et al. 2012); Algorithm 1 uses prefix sums for the
 // work histogram and for the count -> offset step.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "engine.h"
@@ -193,6 +194,45 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const __grid_con
     }
 }
 
+// Packed sort keys: the varying low bits of every column (column 0 most significant)
+// concatenated into one 64-bit key, held as one (width <= 32) or two uint32 columns.
+struct PackSpec {
+    uint32_t arity, kcols;
+    uint32_t width[kMaxArity];      // varying low bits of each column
+    uint32_t high[kMaxArity];       // the constant bits above them (from the first row)
+};
+
+__global__ void k_pack_keys(const __grid_constant__ TableView t, const __grid_constant__ PackSpec S,
+                            uint32_t* __restrict__ khi, uint32_t* __restrict__ klo) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < t.n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = 0;
+        for (uint32_t c = 0; c < S.arity; c++) {
+            const uint32_t w = S.width[c];
+            if (!w) continue;
+            k = (k << w) | (uint64_t)(t.col[c][i] & (w == 32 ? 0xFFFFFFFFu : (1u << w) - 1u));
+        }
+        if (S.kcols == 2) {
+            khi[i] = (uint32_t)(k >> 32);
+            klo[i] = (uint32_t)k;
+        } else {
+            klo[i] = (uint32_t)k;
+        }
+    }
+}
+
+__global__ void k_unpack_keys(const uint32_t* __restrict__ khi, const uint32_t* __restrict__ klo, uint64_t n,
+                              const __grid_constant__ PackSpec S, const __grid_constant__ TableView t) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = S.kcols == 2 ? ((uint64_t)khi[i] << 32) | klo[i] : klo[i];
+        for (int c = (int)S.arity - 1; c >= 0; c--) {
+            const uint32_t w = S.width[c];
+            const uint32_t low = w ? (uint32_t)(k & (w == 32 ? 0xFFFFFFFFull : ((1ull << w) - 1))) : 0u;
+            t.col[c][i] = S.high[c] | low;
+            k = w == 64 ? 0 : (k >> w);
+        }
+    }
+}
+
 // ------------------------------------------------------------- compaction
 
 constexpr int kCompThreads = 256;
@@ -280,6 +320,27 @@ __global__ void k_absent_write(const __grid_constant__ TableView in, const __gri
     }
 }
 
+// Unordered variant (one pass): each warp appends its absent rows at an offset taken from
+// one global counter with a single atomic; rows keep no particular order.
+__global__ void k_absent_append(const __grid_constant__ TableView in, const __grid_constant__ AtomView full,
+                                const __grid_constant__ TableView out, unsigned long long* __restrict__ counter) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < kCompItems; j++) {
+        const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+        const bool f = absent_row_warp(full, in, i, i < in.n);
+        const unsigned ball = __ballot_sync(kFull, f);
+        if (!ball) continue;
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(counter, (unsigned long long)__popc(ball));
+        at = __shfl_sync(kFull, at, 0);
+        if (f) {
+            const uint64_t o = at + __popc(ball & ((1u << lane) - 1));
+            for (uint32_t c = 0; c < in.arity; c++) out.col[c][o] = in.col[c][i];
+        }
+    }
+}
+
 template <class Pred>
 __global__ void k_flag_count(const __grid_constant__ Pred pred, uint64_t n, uint64_t* __restrict__ block_count) {
     const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
@@ -312,7 +373,8 @@ __global__ void k_flag_write(const __grid_constant__ Pred pred, const __grid_con
 // ------------------------------------------------------------------ merge
 
 constexpr int kMergeThreads = 256;
-constexpr int kMergeItems = 8;
+constexpr int kMergeItems = 4;                            // output rows per thread
+constexpr int kMergeTile = kMergeThreads * kMergeItems;   // output rows per CTA
 
 // lexicographic a[i] < b[j]
 __device__ __forceinline__ bool row_less(const TableView& a, uint64_t i, const TableView& b, uint64_t j) {
@@ -323,28 +385,69 @@ __device__ __forceinline__ bool row_less(const TableView& a, uint64_t i, const T
     return false;
 }
 
-__global__ void k_merge(const __grid_constant__ TableView a, const __grid_constant__ TableView b,
-                        const __grid_constant__ TableView out) {
-    const uint64_t total = a.n + b.n;
-    const uint64_t diag = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kMergeItems;
-    if (diag >= total) return;
-    // merge path: number of a-rows among the first `diag` outputs (a first on ties)
+// Merge path (Green et al., the paper's Section 4 Merge): the number of a-rows among the first
+// `diag` rows of merge(a, b), a first on ties.
+__device__ __forceinline__ uint64_t merge_split(const TableView& a, const TableView& b, uint64_t diag) {
     uint64_t lo = diag > b.n ? diag - b.n : 0, hi = diag < a.n ? diag : a.n;
     while (lo < hi) {
-        uint64_t mid = (lo + hi) >> 1;
+        const uint64_t mid = (lo + hi) >> 1;
         if (!row_less(b, diag - 1 - mid, a, mid)) lo = mid + 1; else hi = mid;
     }
-    uint64_t i = lo, j = diag - lo;
-    const uint64_t end = min(diag + kMergeItems, total);
-    for (uint64_t k = diag; k < end; k++) {
-        bool take_a = j >= b.n || (i < a.n && !row_less(b, j, a, i));
-        if (take_a) {
-            for (uint32_t c = 0; c < a.arity; c++) out.col[c][k] = a.col[c][i];
-            i++;
-        } else {
-            for (uint32_t c = 0; c < a.arity; c++) out.col[c][k] = b.col[c][j];
-            j++;
-        }
+    return lo;
+}
+
+// Rows x < y of the staged window (column c of row r at s[c * kMergeTile + r]).
+__device__ __forceinline__ bool staged_less(const uint32_t* s, uint32_t arity, uint32_t x, uint32_t y) {
+    for (uint32_t c = 0; c < arity; c++) {
+        const uint32_t u = s[c * kMergeTile + x], v = s[c * kMergeTile + y];
+        if (u != v) return u < v;
+    }
+    return false;
+}
+
+// One CTA per kMergeTile output rows: two threads find the tile's merge-path split at both
+// ends, the CTA stages the a- and b-windows in shared memory with coalesced loads, each thread
+// merges its kMergeItems outputs from shared memory into a staged output tile, and the tile is
+// written back with coalesced stores (every input and output row crosses HBM once).
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__ TableView a,
+                                                         const __grid_constant__ TableView b,
+                                                         const __grid_constant__ TableView out) {
+    extern __shared__ uint32_t smem[];
+    __shared__ uint64_t s_split[2];
+    const uint32_t arity = a.arity;
+    uint32_t* sin = smem;                                  // arity x kMergeTile: a-window, then b-window
+    uint32_t* sout = smem + (size_t)arity * kMergeTile;    // arity x kMergeTile: merged tile
+    const uint64_t total = a.n + b.n;
+    const uint64_t d0 = (uint64_t)blockIdx.x * kMergeTile, d1 = min(d0 + kMergeTile, total);
+    if (threadIdx.x < 2) s_split[threadIdx.x] = merge_split(a, b, threadIdx.x ? d1 : d0);
+    __syncthreads();
+    const uint64_t i0 = s_split[0], i1 = s_split[1];
+    const uint64_t j0 = d0 - i0;
+    const uint32_t na = (uint32_t)(i1 - i0), n = (uint32_t)(d1 - d0), nb = n - na;
+    for (uint32_t c = 0; c < arity; c++) {
+        const uint32_t* ac = a.col[c] + i0;
+        const uint32_t* bc = b.col[c] + j0;
+        for (uint32_t t = threadIdx.x; t < n; t += kMergeThreads)
+            sin[c * kMergeTile + t] = t < na ? ac[t] : bc[t - na];
+    }
+    __syncthreads();
+    const uint32_t dd = min((uint32_t)threadIdx.x * kMergeItems, n);
+    uint32_t lo = dd > nb ? dd - nb : 0, hi = min(dd, na);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (!staged_less(sin, arity, na + (dd - 1 - mid), mid)) lo = mid + 1; else hi = mid;
+    }
+    uint32_t ia = lo, ib = dd - lo;
+    const uint32_t end = min(dd + kMergeItems, n);
+    for (uint32_t k = dd; k < end; k++) {
+        const bool take_a = ib >= nb || (ia < na && !staged_less(sin, arity, na + ib, ia));
+        const uint32_t src = take_a ? ia++ : na + ib++;
+        for (uint32_t c = 0; c < arity; c++) sout[c * kMergeTile + k] = sin[c * kMergeTile + src];
+    }
+    __syncthreads();
+    for (uint32_t c = 0; c < arity; c++) {
+        uint32_t* oc = out.col[c] + d0;
+        for (uint32_t t = threadIdx.x; t < n; t += kMergeThreads) oc[t] = sout[c * kMergeTile + t];
     }
 }
 
@@ -444,7 +547,7 @@ void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev, bool i
     scan_impl<uint32_t>(E, data, n, inclusive, total_dev);
 }
 
-void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out) {
+void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out, bool allow_pack) {
     int passes = 0;
     const uint64_t n = t.n;
     if (n > 1) {
@@ -459,6 +562,53 @@ void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out) {
         uint32_t hbits[kMaxArity];
         const uint64_t* hb = E.readback(bits.p, kMaxArity / 2);
         memcpy(hbits, hb, sizeof(uint32_t) * t.arity);
+        // Rows whose varying bits fit in 64 bits are sorted as one packed key (one or two
+        // columns instead of all of them, and no pass over constant bits), then unpacked
+        // in place: the same order, fewer bytes per pass.
+        uint32_t wsum = 0;
+        PackSpec S;
+        memset(&S, 0, sizeof(S));
+        S.arity = t.arity;
+        for (uint32_t c = 0; c < t.arity; c++) {
+            S.width[c] = hbits[c] ? 32u - (uint32_t)__builtin_clz(hbits[c]) : 0u;
+            wsum += S.width[c];
+        }
+        S.kcols = wsum > 32 ? 2 : 1;
+        if (allow_pack && t.arity >= 2 && wsum <= 64 && S.kcols < t.arity) {
+            uint32_t first[kMaxArity];
+            for (uint32_t c = 0; c < t.arity; c++)
+                DL_CUDA(cudaMemcpyAsync(first + c, t.col[c], sizeof(uint32_t), cudaMemcpyDeviceToHost, E.stream));
+            E.sync();
+            for (uint32_t c = 0; c < t.arity; c++)
+                S.high[c] = S.width[c] == 32 ? 0u : (first[c] & ~((1u << S.width[c]) - 1u));
+            auto keys = E.array<uint32_t>(4 * n);   // key columns and their sort buffers
+            TableView kt, kt2;
+            memset(&kt, 0, sizeof(kt));
+            memset(&kt2, 0, sizeof(kt2));
+            kt.arity = kt2.arity = S.kcols;
+            kt.n = kt2.n = n;
+            for (uint32_t c = 0; c < S.kcols; c++) {
+                kt.col[c] = keys.p + (uint64_t)c * n;
+                kt2.col[c] = keys.p + (uint64_t)(2 + c) * n;
+            }
+            uint32_t* khi = S.kcols == 2 ? kt.col[0] : nullptr;
+            uint32_t* klo = kt.col[S.kcols - 1];
+            {
+                KernelScope ks(E, DL_K_SORT, (4ull * t.arity + 4ull * S.kcols) * n);
+                k_pack_keys<<<grid_for(n, 256), 256, 0, E.stream>>>(t, S, khi, klo);
+                DL_CHECK_LAUNCH();
+            }
+            radix_sort_rows(E, kt, kt2, &passes, false);
+            khi = S.kcols == 2 ? kt.col[0] : nullptr;
+            klo = kt.col[S.kcols - 1];
+            {
+                KernelScope ks(E, DL_K_SORT, (4ull * t.arity + 4ull * S.kcols) * n);
+                k_unpack_keys<<<grid_for(n, 256), 256, 0, E.stream>>>(khi, klo, n, S, t);
+                DL_CHECK_LAUNCH();
+            }
+            if (passes_out) *passes_out = passes;
+            return;
+        }
         const uint32_t ntiles = (uint32_t)((n + kSortTile - 1) / kSortTile);
         auto hist = E.array<uint32_t>((uint64_t)kRadix * ntiles);
         for (int c = (int)t.arity - 1; c >= 0; c--) {
@@ -511,9 +661,20 @@ uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const
     return total;
 }
 
-uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const TableView& out) {
+uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const TableView& out, bool keep_order) {
     const uint64_t n = in.n;
     if (n == 0) return 0;
+    if (!keep_order) {
+        auto cnt = E.array<uint64_t>(1);
+        DL_CUDA(cudaMemsetAsync(cnt.p, 0, 8, E.stream));
+        {
+            KernelScope ks(E, DL_K_DELTA, 4ull * in.arity * n);
+            k_absent_append<<<(unsigned)((n + kCompTile - 1) / kCompTile), kCompThreads, 0, E.stream>>>(
+                in, full, out, (unsigned long long*)cnt.p);
+            DL_CHECK_LAUNCH();
+        }
+        return E.readback(cnt.p, 1)[0];
+    }
     const uint64_t nb = (n + kCompTile - 1) / kCompTile;
     auto cnt = E.array<uint64_t>(nb + 1);
     const uint64_t rowb = 4ull * in.arity;
@@ -535,9 +696,19 @@ uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const
 void merge_rows(Engine& E, const TableView& a, const TableView& b, const TableView& out) {
     const uint64_t total = a.n + b.n;
     if (!total) return;
-    const uint64_t threads = (total + kMergeItems - 1) / kMergeItems;
+    const size_t smem = sizeof(uint32_t) * 2ull * a.arity * kMergeTile;
+    // the kernel's dynamic shared memory limit, raised once per device (setting it twice is harmless)
+    static std::atomic<uint64_t> attr_set{0};
+    const uint64_t bit = 1ull << (E.device & 63);
+    if (!(attr_set.load() & bit)) {
+        DL_CUDA(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(uint32_t) * 2ull * kMaxArity * kMergeTile)));
+        attr_set.fetch_or(bit);
+    }
+    const uint64_t tiles = (total + kMergeTile - 1) / kMergeTile;
+    if (tiles >= (1ull << 31)) throw Error(DL_ERR_CAPACITY, "merge of 2^31 tiles or more");
     KernelScope ks(E, DL_K_MERGE, 8ull * a.arity * total);
-    k_merge<<<(unsigned)((threads + kMergeThreads - 1) / kMergeThreads), kMergeThreads, 0, E.stream>>>(a, b, out);
+    k_merge<<<(unsigned)tiles, kMergeThreads, smem, E.stream>>>(a, b, out);
     DL_CHECK_LAUNCH();
 }
 

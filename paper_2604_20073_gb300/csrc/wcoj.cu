@@ -327,6 +327,33 @@ __global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count(const __grid_con
     if (threadIdx.x == 0) P.block_count[blockIdx.x] = total;
 }
 
+// Count pass of a count sink's rule in the batched form: every survivor's row hash (over the
+// head's columns after the instance id, numbered from 0, so that it equals the digest of the
+// instance evaluated alone) goes to its instance's accumulators [count, sum, xor].
+template <bool F>
+__global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count_inst(const __grid_constant__ LevelParams P) {
+    uint64_t tlo, thi, e0, e1;
+    tile_bounds(P, tlo, thi);
+    tile_entries(P, tlo, thi, e0, e1);
+    unsigned long long cnt = 0;
+    Unit U;
+    for (uint64_t u = tlo + threadIdx.x; u < thi; u += blockDim.x) {
+        if (!eval_unit<F>(P, u, e0, e1, U)) continue;
+        cnt++;
+        uint64_t h = kTupleHashSeed;
+        for (uint32_t c = 1; c < P.head_arity; c++) {
+            const int pos = P.head_pos[c];
+            h = tuple_hash_step(h, pos < 0 ? P.head_const[c] : value_at(P, U, pos), c - 1);
+        }
+        unsigned long long* d = P.digest + 3ull * __ldg(P.fval[0] + U.e);
+        atomicAdd(d, 1ull);
+        atomicAdd(d + 1, (unsigned long long)h);
+        atomicXor(d + 2, (unsigned long long)h);
+    }
+    const unsigned long long total = block_sum(cnt);
+    if (threadIdx.x == 0) P.block_count[blockIdx.x] = total;
+}
+
 __device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t& total) {
     __shared__ uint32_t ws[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1154,9 +1181,12 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
         r.bc = E.array<uint64_t>(r.ncounts + 1);
         P.tile = tile;
         P.block_count = (unsigned long long*)r.bc.p;
+        const bool per_inst = P.mode == MODE_COUNT && E.instances;   // batched count sink
+        if (per_inst) wmk = r.wm = false;
         if (P.mode == MODE_COUNT) {
-            r.dg = E.array<uint64_t>(3);
-            DL_CUDA(cudaMemsetAsync(r.dg.p, 0, 24, E.stream));
+            const uint64_t words = per_inst ? 3ull * E.instances : 3;
+            r.dg = E.array<uint64_t>(words);
+            DL_CUDA(cudaMemsetAsync(r.dg.p, 0, 8 * words, E.stream));
             P.digest = (unsigned long long*)r.dg.p;
         }
         cudaEvent_t a = nullptr, b = nullptr;
@@ -1167,7 +1197,9 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
         }
         {
             KernelScope ks(E, DL_K_JOIN_COUNT, 4 * Tmin + (entry_bytes + 9) * nF, 1, Tmin, nF);
-            if (wmk) DL_NS_DISPATCH(k_wcoj_count_wm, P.nsrc, filt, (unsigned)r.ntiles, E.stream, P);
+            if (per_inst && filt) k_wcoj_count_inst<true><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
+            else if (per_inst) k_wcoj_count_inst<false><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
+            else if (wmk) DL_NS_DISPATCH(k_wcoj_count_wm, P.nsrc, filt, (unsigned)r.ntiles, E.stream, P);
             else if (filt) k_wcoj_count<true><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
             else k_wcoj_count<false><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
             DL_CHECK_LAUNCH();
@@ -1220,11 +1252,27 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
     };
 
     if (last && count_sink) {
-        const uint64_t* d = E.readback(cr.dg.p, 3);
-        head.sink_count += d[0];
-        head.sink_digest[0] += d[1];
-        head.sink_digest[1] ^= d[2];
-        E.count_rows += d[0];
+        if (E.instances) {
+            std::vector<uint64_t> d(3ull * E.instances);
+            DL_CUDA(cudaMemcpyAsync(d.data(), cr.dg.p, 8 * d.size(), cudaMemcpyDeviceToHost, E.stream));
+            E.sync();
+            head.sink_inst.resize(d.size(), 0);
+            for (uint64_t i = 0; i < E.instances; i++) {
+                head.sink_inst[3 * i] += d[3 * i];
+                head.sink_inst[3 * i + 1] += d[3 * i + 1];
+                head.sink_inst[3 * i + 2] ^= d[3 * i + 2];
+                head.sink_count += d[3 * i];
+                head.sink_digest[0] += d[3 * i + 1];
+                head.sink_digest[1] ^= d[3 * i + 2];
+                E.count_rows += d[3 * i];
+            }
+        } else {
+            const uint64_t* d = E.readback(cr.dg.p, 3);
+            head.sink_count += d[0];
+            head.sink_digest[0] += d[1];
+            head.sink_digest[1] ^= d[2];
+            E.count_rows += d[0];
+        }
         E.phase_end(0);
         return;
     }

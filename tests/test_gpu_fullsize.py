@@ -85,6 +85,23 @@ def test_sampled_roots_match_oracle(edges):
     assert len(got["TriR"]) > 1000 and len(got["Q4R"]) > 100
 
 
+def test_heavy_key_q4_roots_match_oracle(edges):
+    """4-cliques rooted at eight heavy keys (degree ranks 1200-1900, about 700-900 rows each:
+    keys with membership bitmaps, whose candidate ranges are split across warps and CTAs),
+    compared by count and digest (count sinks on both sides)."""
+    e = edges
+    deg = np.bincount(e[:, 0], minlength=1 << 20)
+    order = np.argsort(-deg, kind="stable")
+    roots = np.sort(order[1200:2000:100]).astype(np.uint32).reshape(-1, 1)
+    assert deg[roots.reshape(-1)].min() >= 512
+    rels = {"E": 2, "Root4": 1, "Q4R": 4}
+    facts = {"E": e, "Root4": roots}
+    got, _, _ = pkg.run_program(rels, facts, Q4_R, {"Q4R": pkg.DL_SINK_COUNT})
+    ref = oracle.evaluate(rels, facts, Q4_R, sinks=["Q4R"])
+    assert got["Q4R"] == ref.digests["Q4R"]
+    assert ref.digests["Q4R"][0] > 1_000_000
+
+
 def test_orientation_invariants_and_agm(edges):
     e = edges
     eo = e[e[:, 0] < e[:, 1]]
