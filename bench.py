@@ -146,9 +146,11 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_for(kernel_kind):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if none
-    of the sources it depends on has changed since the counters were taken."""
+def profile_counters(kernel_kind):
+    """DRAM bytes and warp instructions per launch of the dominant kernel at full size, from
+    the committed ncu summary (taken on a smaller graph and scaled by the launch's
+    algorithmic units), if the kernel sources have not changed since the counters were
+    taken; else None."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
@@ -158,7 +160,7 @@ def traffic_for(kernel_kind):
             src = open(os.path.join(ROOT, "paper_2604_20073_gb300", "csrc", name), "rb").read()
             if hashlib.sha256(src).hexdigest() != sha:
                 return None
-        return ent["dram_bytes_per_launch_fullsize"]
+        return ent
     except Exception:
         return None
 
@@ -778,10 +780,26 @@ def main():
     top_bytes = stats[-1]["top"]["alg_bytes"]
     dom = stats[-1]["top"]["kind"]
     achieved = top_bytes / (top_ms / 1e3) / 1e9
+    prof = profile_counters(dom)
+    top_units = stats[-1]["top"]["units"]
+    scale_units = (top_units / prof["units_captured"]) if prof else None
+    traffic = int(prof["dram_bytes_per_launch_captured"] * scale_units) if prof else None
+    issue = None
+    if prof and clk and clk.get("sm_mhz"):
+        # warp instructions issued / (152 SMs x 4 schedulers x clock x launch time): the
+        # kernel's issue-rate roofline (one instruction per scheduler per cycle)
+        inst = prof["inst_executed_captured"] * scale_units
+        slots = 152 * 4 * clk["sm_mhz"] * 1e6 * (top_ms / 1e3)
+        issue = {"warp_instructions": int(inst), "issue_slots": int(slots), "frac": inst / slots,
+                 "source": "ncu smsp__inst_executed.sum on a smaller graph, scaled by algorithmic units"}
     roofline = {"bound": "hbm", "kernel": f"{dom} (longest launch: Q4 last-level count)", "achieved": achieved,
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "traffic": traffic_for(dom), "alg_bytes_per_launch": top_bytes, "avg_launch_ms": top_ms,
+                "traffic": traffic, "traffic_frac": (traffic / (top_ms / 1e3) / 1e9 / peak) if traffic else None,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum on a smaller graph, scaled by "
+                                   "algorithmic units" if traffic else None),
+                "issue": issue, "alg_units_per_launch": top_units,
+                "alg_bytes_per_launch": top_bytes, "avg_launch_ms": top_ms,
                 "share_of_step": top_ms / ms,
                 "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in agg.items() if v["launches"]}}
 
