@@ -200,6 +200,10 @@ Index sort_into_index(Engine& E, DevPtr buf, TableView t, const Perm& perm, uint
     return ix;
 }
 
+// Sorted distinct rows of a raw table as a new index: the packed-key path when the rows'
+// varying bits fit in 64 bits, else sort + adjacent unique.
+Index sort_unique_index(Engine& E, DevPtr buf, TableView t, const Perm& perm, uint32_t arity, uint64_t stride);
+
 void build_roots(Engine& E, Index& ix, bool needed) {
     ix.root.reset();
     ix.rootV = 0;
@@ -546,11 +550,25 @@ Index union_sorted(Engine& E, const Index& a, const Index& b) {
 }
 
 // Drop rows already in full from a raw output part, then sort it and drop duplicates.
+Index sort_unique_index(Engine& E, DevPtr buf, TableView t, const Perm& perm, uint32_t arity, uint64_t stride) {
+    if (t.n > 1) {
+        Index out;
+        E.phase_begin(1);
+        const bool done = sort_unique_packed(E, t, [&](uint64_t m) {
+            out = make_index(E, arity, perm, m);
+            return table_of(out);
+        });
+        E.phase_end(1);
+        if (done) return out;
+    }
+    Index sorted = sort_into_index(E, buf, t, perm, arity, stride);
+    return compute_delta(E, sorted, empty_index(arity, perm), perm, arity, false);
+}
+
 Index reduce_part(Engine& E, Relation& R, DevPtr buf, TableView t) {
     uint64_t stride = 0;
     auto f = prefilter(E, R, buf, t, stride);
-    Index sorted = sort_into_index(E, f.first, f.second, identity_perm(), R.arity, stride);
-    return compute_delta(E, sorted, empty_index(R.arity, identity_perm()), identity_perm(), R.arity, false);
+    return sort_unique_index(E, f.first, f.second, identity_perm(), R.arity, stride);
 }
 
 // Turn one round's join outputs for relation R into its new delta; merge into full.
@@ -598,7 +616,7 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
         jo.owners.clear();
         uint64_t stride = 0;
         auto f = prefilter(E, R, buf, t, stride);
-        newrows = sort_into_index(E, f.first, f.second, identity_perm(), R.arity, stride);
+        d = sort_unique_index(E, f.first, f.second, identity_perm(), R.arity, stride);
         filtered = true;
     }
     if (!d.cols && d.n == 0) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -169,6 +170,11 @@ void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev, bool i
 
 // Sort the rows of t (arity columns, n rows) lexicographically, col[0] most significant.
 // tmp must have the same shape; on return t holds the sorted rows (buffers may be swapped).
+// Sorted distinct rows of t written to the table alloc_out(count) returns, through packed
+// keys (sorted, deduplicated, unpacked once); false (nothing done) when the rows' varying
+// bits do not fit in 64 bits or packing would not shrink them.
+bool sort_unique_packed(Engine& E, const TableView& t, const std::function<TableView(uint64_t)>& alloc_out);
+
 // allow_pack: rows whose varying bits fit in 64 bits are sorted as packed keys.
 void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out, bool allow_pack = true);
 

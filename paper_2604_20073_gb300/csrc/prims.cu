@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <functional>
 
 #include "engine.h"
 
@@ -370,6 +371,47 @@ __global__ void k_flag_write(const __grid_constant__ Pred pred, const __grid_con
     }
 }
 
+// Distinct packed keys (sorted): a row is kept when its key differs from the previous one.
+__device__ __forceinline__ bool key_starts(const uint32_t* khi, const uint32_t* klo, uint64_t i) {
+    return i == 0 || klo[i] != klo[i - 1] || (khi && khi[i] != khi[i - 1]);
+}
+
+__global__ void k_key_distinct_count(const uint32_t* __restrict__ khi, const uint32_t* __restrict__ klo, uint64_t n,
+                                     uint64_t* __restrict__ block_count) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    uint64_t c = 0;
+    for (int j = 0; j < kCompItems; j++) {
+        const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+        if (i < n && key_starts(khi, klo, i)) c++;
+    }
+    uint64_t total;
+    block_exclusive_scan(c, total);
+    if (threadIdx.x == 0) block_count[blockIdx.x] = total;
+}
+
+__global__ void k_key_distinct_write(const uint32_t* __restrict__ khi, const uint32_t* __restrict__ klo, uint64_t n,
+                                     const __grid_constant__ PackSpec S, const __grid_constant__ TableView out,
+                                     const uint64_t* __restrict__ block_off) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    uint64_t run = block_off[blockIdx.x];
+    for (int j = 0; j < kCompItems; j++) {
+        const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+        const uint32_t f = (i < n && key_starts(khi, klo, i)) ? 1u : 0u;
+        uint32_t total;
+        const uint32_t pos = block_exclusive_scan(f, total);
+        if (f) {
+            uint64_t k = S.kcols == 2 ? ((uint64_t)khi[i] << 32) | klo[i] : klo[i];
+            for (int c = (int)S.arity - 1; c >= 0; c--) {
+                const uint32_t w = S.width[c];
+                const uint32_t low = w ? (uint32_t)(k & (w == 32 ? 0xFFFFFFFFull : ((1ull << w) - 1))) : 0u;
+                out.col[c][run + pos] = S.high[c] | low;
+                k >>= w;
+            }
+        }
+        run += total;
+    }
+}
+
 // ------------------------------------------------------------------ merge
 
 constexpr int kMergeThreads = 256;
@@ -634,6 +676,70 @@ void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out, b
         }
     }
     if (passes_out) *passes_out = passes;
+}
+
+bool sort_unique_packed(Engine& E, const TableView& t, const std::function<TableView(uint64_t)>& alloc_out) {
+    const uint64_t n = t.n;
+    if (n < 2 || t.arity < 2) return false;
+    if (n >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "sort of 2^32 rows or more");
+    auto bits = E.array<uint32_t>(kMaxArity);
+    DL_CUDA(cudaMemsetAsync(bits.p, 0, sizeof(uint32_t) * kMaxArity, E.stream));
+    for (uint32_t c = 0; c < t.arity; c++) {
+        KernelScope ks(E, DL_K_SORT, 4 * n);
+        k_varying_bits<<<grid_for(n, 256), 256, 0, E.stream>>>(t.col[c], n, bits.p + c);
+        DL_CHECK_LAUNCH();
+    }
+    uint32_t hbits[kMaxArity];
+    memcpy(hbits, E.readback(bits.p, kMaxArity / 2), sizeof(uint32_t) * t.arity);
+    PackSpec S;
+    memset(&S, 0, sizeof(S));
+    S.arity = t.arity;
+    uint32_t wsum = 0;
+    for (uint32_t c = 0; c < t.arity; c++) {
+        S.width[c] = hbits[c] ? 32u - (uint32_t)__builtin_clz(hbits[c]) : 0u;
+        wsum += S.width[c];
+    }
+    S.kcols = wsum > 32 ? 2 : 1;
+    if (wsum > 64 || S.kcols >= t.arity) return false;
+    uint32_t first[kMaxArity];
+    for (uint32_t c = 0; c < t.arity; c++)
+        DL_CUDA(cudaMemcpyAsync(first + c, t.col[c], sizeof(uint32_t), cudaMemcpyDeviceToHost, E.stream));
+    E.sync();
+    for (uint32_t c = 0; c < t.arity; c++) S.high[c] = S.width[c] == 32 ? 0u : (first[c] & ~((1u << S.width[c]) - 1u));
+    auto keys = E.array<uint32_t>(4 * n);
+    TableView kt, kt2;
+    memset(&kt, 0, sizeof(kt));
+    memset(&kt2, 0, sizeof(kt2));
+    kt.arity = kt2.arity = S.kcols;
+    kt.n = kt2.n = n;
+    for (uint32_t c = 0; c < S.kcols; c++) {
+        kt.col[c] = keys.p + (uint64_t)c * n;
+        kt2.col[c] = keys.p + (uint64_t)(2 + c) * n;
+    }
+    {
+        KernelScope ks(E, DL_K_SORT, (4ull * t.arity + 4ull * S.kcols) * n);
+        k_pack_keys<<<grid_for(n, 256), 256, 0, E.stream>>>(t, S, S.kcols == 2 ? kt.col[0] : nullptr, kt.col[S.kcols - 1]);
+        DL_CHECK_LAUNCH();
+    }
+    radix_sort_rows(E, kt, kt2, nullptr, false);
+    const uint32_t* khi = S.kcols == 2 ? kt.col[0] : nullptr;
+    const uint32_t* klo = kt.col[S.kcols - 1];
+    const uint64_t nb = (n + kCompTile - 1) / kCompTile;
+    auto cnt = E.array<uint64_t>(nb + 1);
+    {
+        KernelScope ks(E, DL_K_DELTA, 8ull * S.kcols * n);
+        k_key_distinct_count<<<(unsigned)nb, kCompThreads, 0, E.stream>>>(khi, klo, n, cnt.p);
+        DL_CHECK_LAUNCH();
+    }
+    scan_u64(E, cnt.p, nb, false, cnt.p + nb);
+    const uint64_t total = E.readback(cnt.p + nb, 1)[0];
+    const TableView out = alloc_out(total);
+    if (total) {
+        KernelScope ks(E, DL_K_DELTA, 8ull * S.kcols * n + 4ull * t.arity * total);
+        k_key_distinct_write<<<(unsigned)nb, kCompThreads, 0, E.stream>>>(khi, klo, n, S, out, cnt.p);
+        DL_CHECK_LAUNCH();
+    }
+    return true;
 }
 
 uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const TableView& out) {

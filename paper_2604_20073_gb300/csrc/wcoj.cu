@@ -66,7 +66,6 @@ struct LevelParams {
     const uint32_t* seg;                  // sibling run of each entry: inclusive segment number
     const uint32_t* segstart;             // first entry of each segment (+ end sentinel)
     unsigned long long* C;                // per entry: W, then inclusive prefix
-    unsigned long long* tmin;             // histogram: sum over entries of the smallest source size
     uint8_t* drv;                         // per entry: driving source
     uint64_t T;
     uint64_t tile;
@@ -86,6 +85,7 @@ struct LevelParams {
     uint32_t head_arity;
     int8_t head_pos[kMaxArity];           // order position of head column, -1 = constant
     int8_t head_lvl;                      // MODE_COUNT: the head column holding the level's variable
+    int8_t head_shared;                   // MODE_COUNT: leading head columns shared by an entry's siblings
     uint32_t head_const[kMaxArity];
     uint32_t* ocol[kMaxArity];
     unsigned long long* digest;           // MODE_COUNT: [count, sum, xor]
@@ -149,34 +149,29 @@ __device__ __forceinline__ const uint32_t* src_range(const LevelParams& P, int s
 }
 
 // Histogram (Algorithm 1, Phase 1, at every level): each entry's work W = the size of its
-// smallest candidate source, which drives the entry.  The sum of W over the entries is the
-// level's algorithmic work (every candidate of the smallest source is examined once).
+// smallest candidate source, which drives the entry.  The sum of W over the entries (the
+// scan's total T) is the level's algorithmic work: every candidate of the smallest source is
+// examined once.
 __global__ void k_wcoj_hist(const __grid_constant__ LevelParams P) {
     const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    unsigned long long w = 0;
-    if (e < P.nF) {
-        unsigned long long best = ~0ull;
-        uint32_t bs = 0;
-        for (uint32_t s = 0; s < P.nsrc; s++) {
-            const int a = P.src_atom[s], d = P.src_depth[s];
-            unsigned long long len;
-            if (a != kVirtual && d == 0) {
-                const AtomView& A = P.atom[a];
-                len = A.n == 0 ? 0 : (A.root ? A.V : A.n);
-            } else {
-                uint32_t lo, hi;
-                src_range(P, (int)s, e, lo, hi);
-                len = hi - lo;
-            }
-            if (len < best) { best = len; bs = s; }
+    if (e >= P.nF) return;
+    unsigned long long best = ~0ull;
+    uint32_t bs = 0;
+    for (uint32_t s = 0; s < P.nsrc; s++) {
+        const int a = P.src_atom[s], d = P.src_depth[s];
+        unsigned long long len;
+        if (a != kVirtual && d == 0) {
+            const AtomView& A = P.atom[a];
+            len = A.n == 0 ? 0 : (A.root ? A.V : A.n);
+        } else {
+            uint32_t lo, hi;
+            src_range(P, (int)s, e, lo, hi);
+            len = hi - lo;
         }
-        w = best == ~0ull ? 0 : best;
-        P.C[e] = w;
-        P.drv[e] = (uint8_t)bs;
+        if (len < best) { best = len; bs = s; }
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if ((threadIdx.x & 31) == 0 && w) atomicAdd(P.tmin, w);
+    P.C[e] = best == ~0ull ? 0 : best;
+    P.drv[e] = (uint8_t)bs;
 }
 
 struct Unit {
@@ -605,12 +600,26 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
         EntryState<NS> S;
         uint32_t r = 0;
         uint64_t hpre = 0;        // MODE_COUNT: row hash over the head columns before head_lvl
+        uint64_t hsh = 0;         // hash of the columns shared by the current sibling run
+        uint32_t run = 0xFFFFFFFFu;
         for (;;) {
             const uint64_t wlo = s_wlo[threadIdx.x >> 5], whi = s_whi[threadIdx.x >> 5];
             const uint32_t stop = (uint32_t)(min(entry_load(P, S, e, wlo), whi) - wlo);
             if (P.mode == MODE_COUNT) {
-                hpre = kTupleHashSeed;
-                for (int c = 0; c < P.head_lvl; c++) hpre = tuple_hash_step(hpre, head_value(P, c, e), c);
+                int c0 = 0;
+                if (P.head_shared > 0) {
+                    const uint32_t g = __ldg(P.seg + e);
+                    if (g != run) {
+                        run = g;
+                        hsh = kTupleHashSeed;
+                        for (int c = 0; c < P.head_shared; c++) hsh = tuple_hash_step(hsh, head_value(P, c, e), c);
+                    }
+                    c0 = P.head_shared;
+                    hpre = hsh;
+                } else {
+                    hpre = kTupleHashSeed;
+                }
+                for (int c = c0; c < P.head_lvl; c++) hpre = tuple_hash_step(hpre, head_value(P, c, e), c);
             }
             for (uint32_t b = r; b < stop; b += 32) {
                 const uint32_t rr = b + lane;
@@ -1128,25 +1137,21 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
     for (uint32_t a = 0; a < plan.natoms; a++) nslots_in += F.slot_of[a] >= 0;
     const uint64_t entry_bytes = 4ull * (lvl + 2 * nslots_in) + (reuse ? 8 : 0);
 
-    // Phase 1: histogram + prefix (C[nF] receives the total, C[nF + 1] the summed smallest
-    // source sizes)
-    auto C = E.array<uint64_t>(nF + 2);
+    // Phase 1: histogram + prefix (C[nF] receives the total)
+    auto C = E.array<uint64_t>(nF + 1);
     auto drv = E.array<uint8_t>(nF);
     P.C = (unsigned long long*)C.p;
-    P.tmin = (unsigned long long*)(C.p + nF + 1);
     P.drv = drv.p;
     E.phase_begin(0);
-    DL_CUDA(cudaMemsetAsync(C.p + nF + 1, 0, sizeof(uint64_t), E.stream));
     {
         KernelScope ks(E, DL_K_JOIN_HIST, (entry_bytes + 9) * nF, 1, 0, nF);
         k_wcoj_hist<<<(unsigned)((nF + 255) / 256), 256, 0, E.stream>>>(P);
         DL_CHECK_LAUNCH();
     }
     scan_u64(E, C.p, nF, true, C.p + nF);
-    const uint64_t* tt = E.readback(C.p + nF, 2);
-    const uint64_t T = tt[0];
+    const uint64_t T = E.readback(C.p + nF, 1)[0];
     // algorithmic work of the level: every candidate of each entry's smallest source
-    const uint64_t Tmin = tt[1];
+    const uint64_t Tmin = T;
     if (T == 0) {
         E.phase_end(0);
         return;
@@ -1168,6 +1173,12 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
         for (uint32_t c = 0; c < P.head_arity; c++)
             if (P.head_pos[c] == (int)lvl) P.head_lvl = (int8_t)c;
         if (P.head_lvl < 0) throw Error(DL_ERR_STATE, "count sink head lacks the last variable");
+        // leading head columns bound above the previous level are equal across a sibling run
+        P.head_shared = 0;
+        if (P.seg && lvl >= 2)
+            while (P.head_shared < P.head_lvl && P.head_pos[P.head_shared] >= 0 &&
+                   P.head_pos[P.head_shared] < (int)lvl - 1)
+                P.head_shared++;
     } else {
         P.mode = last ? MODE_HEAD : MODE_FRONTIER;
     }
