@@ -796,8 +796,9 @@ def main():
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "traffic": traffic, "traffic_frac": (traffic / (top_ms / 1e3) / 1e9 / peak) if traffic else None,
-                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum on a smaller graph, scaled by "
-                                   "algorithmic units" if traffic else None),
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum on the scale-18 graph, scaled by "
+                                   "algorithmic units (a lower bound: the heavy-key bitmaps fit L2 better at scale 18)"
+                                   if traffic else None),
                 "issue": issue, "alg_units_per_launch": top_units,
                 "alg_bytes_per_launch": top_bytes, "avg_launch_ms": top_ms,
                 "share_of_step": top_ms / ms,

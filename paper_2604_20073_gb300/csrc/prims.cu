@@ -148,17 +148,24 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ key, uint64_t n, uint3
 }
 
 // Stable scatter: warp w of the block owns the contiguous rows [base + w*32*I, base + (w+1)*32*I);
-// iteration j handles row base + w*32*I + j*32 + lane, so (j, lane) order is row order.
+// iteration j handles row base + w*32*I + j*32 + lane, so (j, lane) order is row order.  Each
+// row's rank within its digit is found with a warp match; the tile's rows are then staged in
+// shared memory in digit order and written out so that consecutive threads store consecutive
+// rows of one digit's run (coalesced), instead of every lane storing to a different run.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const __grid_constant__ TableView src,
                                                                 const __grid_constant__ TableView dst, int keycol,
                                                                 uint32_t shift, const uint32_t* __restrict__ offs,
                                                                 uint32_t ntiles) {
+    extern __shared__ uint32_t stage[];                  // arity x kSortTile rows, digit order
     __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    __shared__ uint32_t lstart[kRadix], gstart[kRadix];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const uint64_t n = src.n;
-    const uint64_t wbase = (uint64_t)blockIdx.x * kSortTile + (uint64_t)warp * 32 * kSortItems;
+    const uint64_t tbase = (uint64_t)blockIdx.x * kSortTile;
+    const uint32_t tn = (uint32_t)min((uint64_t)kSortTile, n - tbase);
+    const uint64_t wbase = tbase + (uint64_t)warp * 32 * kSortItems;
     const unsigned lt = (1u << lane) - 1;
     uint32_t rank[kSortItems], dig[kSortItems];
     const uint32_t* key = src.col[keycol];
@@ -176,22 +183,34 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const __grid_con
         dig[j] = d;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-        uint32_t run = offs[(uint64_t)d * ntiles + blockIdx.x];
+    // per digit (one per thread): the warps' prefix within the digit, the tile's digit total
+    uint32_t tot = 0;
+    {
+        const int d = threadIdx.x;
         for (int w = 0; w < kSortWarps; w++) {
-            uint32_t c = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += c;
+            const uint32_t c = wcnt[w][d];
+            wcnt[w][d] = tot;
+            tot += c;
         }
+        gstart[d] = offs[(uint64_t)d * ntiles + blockIdx.x];
     }
+    uint32_t all;
+    const uint32_t ls = block_exclusive_scan(tot, all);   // the digit's first row in the tile
+    lstart[threadIdx.x] = ls;
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kSortItems; j++) {
         uint64_t i = wbase + (uint64_t)j * 32 + lane;
         if (i < n) {
-            uint64_t to = (uint64_t)wcnt[warp][dig[j]] + rank[j];
-            for (uint32_t c = 0; c < src.arity; c++) dst.col[c][to] = src.col[c][i];
+            const uint32_t lp = lstart[dig[j]] + wcnt[warp][dig[j]] + rank[j];
+            for (uint32_t c = 0; c < src.arity; c++) stage[c * kSortTile + lp] = src.col[c][i];
         }
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < tn; p += kSortThreads) {
+        const uint32_t d = (stage[keycol * kSortTile + p] >> shift) & (kRadix - 1);
+        const uint64_t to = (uint64_t)gstart[d] + (p - lstart[d]);
+        for (uint32_t c = 0; c < src.arity; c++) dst.col[c][to] = stage[c * kSortTile + p];
     }
 }
 
@@ -415,7 +434,7 @@ __global__ void k_key_distinct_write(const uint32_t* __restrict__ khi, const uin
 // ------------------------------------------------------------------ merge
 
 constexpr int kMergeThreads = 256;
-constexpr int kMergeItems = 4;                            // output rows per thread
+constexpr int kMergeItems = 8;                            // output rows per thread
 constexpr int kMergeTile = kMergeThreads * kMergeItems;   // output rows per CTA
 
 // lexicographic a[i] < b[j]
@@ -447,23 +466,29 @@ __device__ __forceinline__ bool staged_less(const uint32_t* s, uint32_t arity, u
     return false;
 }
 
-// One CTA per kMergeTile output rows: two threads find the tile's merge-path split at both
-// ends, the CTA stages the a- and b-windows in shared memory with coalesced loads, each thread
-// merges its kMergeItems outputs from shared memory into a staged output tile, and the tile is
-// written back with coalesced stores (every input and output row crosses HBM once).
+// Merge-path splits of every tile boundary (one thread each, all searches in parallel).
+__global__ void k_merge_splits(const __grid_constant__ TableView a, const __grid_constant__ TableView b,
+                               uint64_t ntiles, uint64_t* __restrict__ split) {
+    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    split[t] = merge_split(a, b, min(t * (uint64_t)kMergeTile, a.n + b.n));
+}
+
+// One CTA per kMergeTile output rows: the CTA stages the a- and b-windows between its two
+// splits in shared memory with coalesced loads, each thread merges its kMergeItems outputs
+// from shared memory into a staged output tile, and the tile is written back with coalesced
+// stores (every input and output row crosses HBM once).
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__ TableView a,
                                                          const __grid_constant__ TableView b,
-                                                         const __grid_constant__ TableView out) {
+                                                         const __grid_constant__ TableView out,
+                                                         const uint64_t* __restrict__ split) {
     extern __shared__ uint32_t smem[];
-    __shared__ uint64_t s_split[2];
     const uint32_t arity = a.arity;
     uint32_t* sin = smem;                                  // arity x kMergeTile: a-window, then b-window
     uint32_t* sout = smem + (size_t)arity * kMergeTile;    // arity x kMergeTile: merged tile
     const uint64_t total = a.n + b.n;
     const uint64_t d0 = (uint64_t)blockIdx.x * kMergeTile, d1 = min(d0 + kMergeTile, total);
-    if (threadIdx.x < 2) s_split[threadIdx.x] = merge_split(a, b, threadIdx.x ? d1 : d0);
-    __syncthreads();
-    const uint64_t i0 = s_split[0], i1 = s_split[1];
+    const uint64_t i0 = split[blockIdx.x], i1 = split[blockIdx.x + 1];
     const uint64_t j0 = d0 - i0;
     const uint32_t na = (uint32_t)(i1 - i0), n = (uint32_t)(d1 - d0), nb = n - na;
     for (uint32_t c = 0; c < arity; c++) {
@@ -592,6 +617,14 @@ void scan_u32(Engine& E, uint32_t* data, uint64_t n, uint64_t* total_dev, bool i
 void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out, bool allow_pack) {
     int passes = 0;
     const uint64_t n = t.n;
+    // the scatter's staging buffer: up to kMaxArity x kSortTile rows (raised once per device)
+    static std::atomic<uint64_t> attr_set{0};
+    const uint64_t bit = 1ull << (E.device & 63);
+    if (!(attr_set.load() & bit)) {
+        DL_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(uint32_t) * kMaxArity * kSortTile)));
+        attr_set.fetch_or(bit);
+    }
     if (n > 1) {
         if (n >= (1ull << 32)) throw Error(DL_ERR_CAPACITY, "sort of 2^32 rows or more");
         auto bits = E.array<uint32_t>(kMaxArity);
@@ -667,7 +700,8 @@ void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out, b
                 TableView dst = tmp;
                 dst.n = n;
                 KernelScope ks(E, DL_K_SORT, (4 + 8ull * t.arity) * n);
-                k_radix_scatter<<<ntiles, kSortThreads, 0, E.stream>>>(t, dst, c, shift, hist.p, ntiles);
+                k_radix_scatter<<<ntiles, kSortThreads, sizeof(uint32_t) * t.arity * kSortTile, E.stream>>>(
+                    t, dst, c, shift, hist.p, ntiles);
                 DL_CHECK_LAUNCH();
                 std::swap(t, tmp);
                 t.n = n;
@@ -813,8 +847,14 @@ void merge_rows(Engine& E, const TableView& a, const TableView& b, const TableVi
     }
     const uint64_t tiles = (total + kMergeTile - 1) / kMergeTile;
     if (tiles >= (1ull << 31)) throw Error(DL_ERR_CAPACITY, "merge of 2^31 tiles or more");
+    auto split = E.array<uint64_t>(tiles + 1);
+    {
+        KernelScope ks(E, DL_K_MERGE, 16ull * (tiles + 1));
+        k_merge_splits<<<(unsigned)((tiles + 1 + 255) / 256), 256, 0, E.stream>>>(a, b, tiles, split.p);
+        DL_CHECK_LAUNCH();
+    }
     KernelScope ks(E, DL_K_MERGE, 8ull * a.arity * total);
-    k_merge<<<(unsigned)tiles, kMergeThreads, smem, E.stream>>>(a, b, out);
+    k_merge<<<(unsigned)tiles, kMergeThreads, smem, E.stream>>>(a, b, out, split.p);
     DL_CHECK_LAUNCH();
 }
 
