@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--no-batched", action="store_true", help="default line without its batched sub-object")
     ap.add_argument("--no-served", action="store_true", help="default line without its served sub-object")
+    ap.add_argument("--no-autotune", action="store_true", help="default line without the autotuner's before/after")
     ap.add_argument("--served-requests", type=int, default=600, help="requests of the default line's served leg")
     return ap.parse_args()
 
@@ -270,7 +271,7 @@ def kernel_rates(kms: dict, kbytes: dict, peak: float) -> dict:
     return out
 
 
-def batched_measure(instances: int, warmup: int, steps: int) -> dict:
+def batched_measure(instances: int, warmup: int, steps: int, autotune: bool = True) -> dict:
     """Batched form: independent TC + Tri programs on R-MAT graphs with edge counts
     log-uniform in [100, 50000] (nodes = edges / 8), evaluated together (one launch per
     stage per group of instances; groups keep every relation under 2^32 rows), against one
@@ -334,6 +335,29 @@ def batched_measure(instances: int, warmup: int, steps: int) -> dict:
     for eng, g in zip(engines, groups):
         for j, i in enumerate(g):
             sizes_b[i] = (eng.size_instance("Tri", j), eng.instance_rounds(j))
+    tuned = None
+    if autotune:
+        # the autotuner on the same engines: one step tunes every (rule, level, size bucket),
+        # the next is timed with the cached choices; results must not change
+        for eng in engines:
+            eng.set_flags(pkg.DL_FLAG_PROFILE | pkg.DL_FLAG_AUTOTUNE)
+        sts = step()
+        tuned_levels = sum(st["tuned_levels"] for st in sts)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sts = step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        same = all(eng.size_instance("Tri", j) == sizes_b[i][0] and eng.instance_rounds(j) == sizes_b[i][1]
+                   for eng, g in zip(engines, groups) for j, i in enumerate(g))
+        choices = engines[0].tune_choices()
+        tuned = {"default_ms": ms, "tuned_ms": a.elapsed_time(b), "levels_tuned": tuned_levels,
+                 "cached_hits_in_timed_step": sum(st["tune_hits"] for st in sts), "identical_results": same,
+                 "choices_group0": [{"tile": c["tile"], "warp_major": c["warp_major"], "count_ms": c["ms"]}
+                                    for c in choices][:24]}
+        for eng in engines:
+            eng.set_flags(pkg.DL_FLAG_PROFILE)
     reach_total = sum(eng.size("Reach") for eng in engines)
     tri_total = sum(eng.size("Tri") for eng in engines)
     rng = np.random.default_rng(5)
@@ -376,7 +400,7 @@ def batched_measure(instances: int, warmup: int, steps: int) -> dict:
             "speedup_vs_per_instance": base_ms / ms, "mismatches_vs_alone": mism,
             "Reach_rows": int(reach_total), "Tri_rows": int(tri_total),
             "rounds_max": max(max(r[1]) for r in sizes_b.values()), "gpu_launches_per_step": launches / steps,
-            "kernels": kernel_rates(kms, kbytes, peak)}
+            "kernels": kernel_rates(kms, kbytes, peak), "autotune": tuned}
 
 
 def run_batched_workload(args):
@@ -761,6 +785,7 @@ def main():
         times.append(a.elapsed_time(b))
         stats.append(st)
     clk = clocks.stop()
+    q4_digest = eng.digest("Q4")
     ms = statistics.mean(times)
     if dist:
         ms = max_over_ranks(ms, dist, dev)
@@ -804,6 +829,29 @@ def main():
                 "share_of_step": top_ms / ms,
                 "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in agg.items() if v["launches"]}}
 
+    # the autotuner (DL_FLAG_AUTOTUNE) on the same engine: a tuning fixpoint, then timed ones
+    autotune = None
+    if not args.no_autotune:
+        eng.set_flags(pkg.DL_FLAG_PROFILE | pkg.DL_FLAG_AUTOTUNE)
+        flush.fill_(1)
+        st_t = step()
+        tms = []
+        for _ in range(max(1, min(3, args.steps))):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tms.append(a.elapsed_time(b))
+        autotune = {"default_ms": ms, "tuned_ms": statistics.mean(tms), "levels_tuned": int(st_t["tuned_levels"]),
+                    "identical_results": st["join_rows"] == stats[-1]["join_rows"] and
+                    eng.digest("Q4") == q4_digest,
+                    "choices": [{"tile": c["tile"], "warp_major": c["warp_major"], "count_ms": c["ms"]}
+                                for c in eng.tune_choices()]}
+        eng.set_flags(pkg.DL_FLAG_PROFILE)
+
     # end to end through the C ABI from pinned host buffers
     e_host = [torch.from_numpy(np.ascontiguousarray(e[:, c])).pin_memory().numpy() for c in range(2)]
     ntri = eng.size("Tri")
@@ -833,7 +881,7 @@ def main():
     batched = served = None
     if not args.no_batched:
         clocks_b = Clocks(local)
-        batched = batched_measure(args.instances, 1, 1)
+        batched = batched_measure(args.instances, 1, 1, autotune=not args.no_autotune)
         batched["clocks"] = clocks_b.stop()
     if not args.no_served:
         clocks_s = Clocks(local)
@@ -860,7 +908,7 @@ def main():
                            "wcoj_tuples_per_s_join_phases": (tuples / (stats[-1]["ms_join"] / 1e3)
                                                              if stats[-1]["ms_join"] > 0 else None)},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-               "batched": batched, "served": served}
+               "autotune": autotune, "batched": batched, "served": served}
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()

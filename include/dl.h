@@ -133,6 +133,10 @@ typedef struct dl_config {
  * Errors: DL_ERR_ARG (bad config), DL_ERR_CUDA (no device / context creation failed). */
 int dl_engine_create(const dl_config* cfg, dl_engine** out);
 
+/* Replace the engine's DL_FLAG_* flags for its later calls (e.g. switch the autotuner or
+ * profiling on between fixpoints).  Errors: DL_ERR_ARG (NULL engine). */
+int dl_engine_set_flags(dl_engine* e, uint32_t flags);
+
 /* Destroy an engine and free every device buffer it owns.  NULL is ignored. */
 void dl_engine_destroy(dl_engine* e);
 
@@ -421,12 +425,16 @@ typedef struct dl_server_config {
     uint64_t default_share;   /* share of a request that states none; 0 = 1 GiB */
 } dl_server_config;
 
-typedef struct dl_rule_spec {
+typedef struct dl_rule_spec {  /* a rule of a request, as dl_rule_add_ex takes it */
     dl_atom head;
     const dl_atom* body;
     uint32_t nbody;
     const uint32_t* var_order;
     uint32_t nvars;
+    const dl_atom* neg;           /* negated atoms (stratified negation), or NULL */
+    uint32_t nneg;
+    const dl_cmp* cmps;           /* comparisons, or NULL */
+    uint32_t ncmp;
 } dl_rule_spec;
 
 typedef struct dl_fact_spec {

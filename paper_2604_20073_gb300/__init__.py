@@ -90,7 +90,8 @@ class dl_server_config(ctypes.Structure):
 
 class dl_rule_spec(ctypes.Structure):
     _fields_ = [("head", dl_atom), ("body", ctypes.POINTER(dl_atom)), ("nbody", ctypes.c_uint32),
-                ("var_order", _u32p), ("nvars", ctypes.c_uint32)]
+                ("var_order", _u32p), ("nvars", ctypes.c_uint32), ("neg", ctypes.POINTER(dl_atom)),
+                ("nneg", ctypes.c_uint32), ("cmps", ctypes.POINTER(dl_cmp)), ("ncmp", ctypes.c_uint32)]
 
 
 class dl_fact_spec(ctypes.Structure):
@@ -163,6 +164,7 @@ _SIGS = {
     "dl_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "dl_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(dl_server_stats)]),
     "dl_tune_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "dl_engine_set_flags": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "dl_program_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "dl_program_destroy": (None, [ctypes.c_void_p]),
     "dl_program_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -449,6 +451,22 @@ class Engine:
                               "entries": st.kernels[i].entries} for i, k in enumerate(KERNEL_KINDS)}
         return out
 
+    def set_flags(self, flags: int):
+        """Replace the engine's DL_FLAG_* flags for its later calls."""
+        self._check(self.lib.dl_engine_set_flags(self.h, flags))
+
+    def tune_choices(self) -> list:
+        """The autotuner's choices so far: [{key, tile, warp_major, ms}]."""
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            p = os.path.join(td, "tune.txt")
+            self.tune_save(p)
+            out = []
+            for line in open(p):
+                k, tile, wm, ms = line.split()
+                out.append({"key": k, "tile": int(tile), "warp_major": wm == "1", "ms": float(ms)})
+            return out
+
     def tune_save(self, path: str):
         """Write the autotuner's choices (DL_FLAG_AUTOTUNE) to a text file."""
         self._check(self.lib.dl_tune_save(self.h, path.encode()))
@@ -545,26 +563,13 @@ class Server:
         sink = (ctypes.c_uint32 * len(names))(*[(sinks or {}).get(n, DL_SINK_STORE) for n in names])
         rs = (dl_rule_spec * len(rules))()
         for k, r in enumerate(rules):
-            var_ids: dict = {}
-
-            def atom(a):
-                rel, terms = a
-                ts = (dl_term * len(terms))()
-                for i, t in enumerate(terms):
-                    if isinstance(t, str):
-                        ts[i].kind, ts[i].id = DL_TERM_VAR, var_ids.setdefault(t, len(var_ids))
-                    else:
-                        ts[i].kind, ts[i].id = DL_TERM_CONST, int(t)
-                keep.append(ts)
-                out = dl_atom()
-                out.rel, out.arity, out.terms = rid[rel], len(terms), ts
-                return out
-            body = (dl_atom * len(r[1]))(*[atom(b) for b in r[1]])
-            head = atom(r[0])
-            order = (ctypes.c_uint32 * len(r[2]))(*[var_ids.get(v, 1023) for v in r[2]])
-            keep += [body, order]
-            rs[k].head, rs[k].body, rs[k].nbody = head, body, len(r[1])
-            rs[k].var_order, rs[k].nvars = order, len(r[2])
+            # body items: atoms, negated atoms ("not", atom) and comparisons (op, a, b)
+            head, batoms, npos, natoms, nneg, carr, ncmp, order, norder, kp = _encode_rule(rid, r[0], r[1], r[2])
+            keep += kp
+            rs[k].head, rs[k].body, rs[k].nbody = head, batoms, npos
+            rs[k].var_order, rs[k].nvars = order, norder
+            rs[k].neg, rs[k].nneg = natoms, nneg
+            rs[k].cmps, rs[k].ncmp = carr, ncmp
         fs = (dl_fact_spec * len(facts))()
         for k, (name, rows) in enumerate(facts.items()):
             rows = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32).reshape(-1, relations[name]))

@@ -1030,6 +1030,10 @@ int dl_engine_create(const dl_config* cfg, dl_engine** out) {
     return DL_OK;
 }
 
+int dl_engine_set_flags(dl_engine* e, uint32_t flags) {
+    return guard(e, [&](Engine& E) { E.flags = flags; });
+}
+
 void dl_engine_destroy(dl_engine* e) {
     if (!e) return;
     Engine* E = reinterpret_cast<Engine*>(e);

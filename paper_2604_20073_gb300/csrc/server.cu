@@ -22,8 +22,9 @@ namespace {
 struct RuleCopy {
     dl_atom head;
     std::vector<dl_term> head_terms;
-    std::vector<dl_atom> body;
-    std::vector<std::vector<dl_term>> body_terms;
+    std::vector<dl_atom> body, neg;
+    std::vector<std::vector<dl_term>> body_terms, neg_terms;
+    std::vector<dl_cmp> cmps;
     std::vector<uint32_t> order;
 };
 
@@ -101,8 +102,10 @@ int evaluate(dl_server* s, cudaStream_t stream, Ticket* t) {
     for (RuleCopy& r : t->rules) {
         r.head.terms = r.head_terms.data();
         for (size_t b = 0; b < r.body.size(); b++) r.body[b].terms = r.body_terms[b].data();
+        for (size_t b = 0; b < r.neg.size(); b++) r.neg[b].terms = r.neg_terms[b].data();
         dl_rule_id rid;
-        rc = dl_rule_add(e, &r.head, r.body.data(), (uint32_t)r.body.size(), r.order.data(), (uint32_t)r.order.size(), &rid);
+        rc = dl_rule_add_ex(e, &r.head, r.body.data(), (uint32_t)r.body.size(), r.neg.data(), (uint32_t)r.neg.size(),
+                            r.cmps.data(), (uint32_t)r.cmps.size(), r.order.data(), (uint32_t)r.order.size(), &rid);
         if (rc != DL_OK) return rc;
     }
     for (FactCopy& f : t->facts)
@@ -235,6 +238,13 @@ int dl_server_submit(dl_server* s, const dl_request* req, uint64_t* ticket) {
             rc.body.push_back(rs.body[b]);
             rc.body_terms.emplace_back(rs.body[b].terms, rs.body[b].terms + rs.body[b].arity);
         }
+        if ((rs.nneg && !rs.neg) || (rs.ncmp && !rs.cmps)) return DL_ERR_ARG;
+        for (uint32_t b = 0; b < rs.nneg; b++) {
+            if (!rs.neg[b].terms) return DL_ERR_ARG;
+            rc.neg.push_back(rs.neg[b]);
+            rc.neg_terms.emplace_back(rs.neg[b].terms, rs.neg[b].terms + rs.neg[b].arity);
+        }
+        if (rs.ncmp) rc.cmps.assign(rs.cmps, rs.cmps + rs.ncmp);
         rc.order.assign(rs.var_order, rs.var_order + rs.nvars);
         t->rules.push_back(std::move(rc));
     }

@@ -1235,8 +1235,13 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
             E.tune_hits++;
         } else {
             CountRun best;
+            // shapes worth timing: a thread per unit decodes every unit's entry (hopeless when
+            // entries average hundreds of units); a warp per entry range idles lanes on entries
+            // of a few units
+            const bool try_striped = T < 256 * nF, try_warp = T >= 4 * nF;
             for (uint32_t tile : {4096u, 16384u, 65536u})
                 for (bool wmk : {false, true}) {
+                    if ((wmk && !try_warp) || (!wmk && !try_striped)) continue;
                     CountRun r = count_with(tile, wmk, true);
                     if (!best.bc.mem || r.ms < best.ms) best = std::move(r);
                 }

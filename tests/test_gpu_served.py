@@ -108,3 +108,23 @@ def test_over_share_request_fails_alone():
         srv.release(ok)
         with pytest.raises(pkg.DatalogError):
             srv.submit(P.TC_TRI_RELS, {"E": small}, P.TC_TRI, share=4 << 30)
+
+
+def test_served_rules_with_negation_and_comparisons():
+    """Requests carry negated atoms and comparisons (dl_rule_spec.neg / .cmps)."""
+    tri_lt = [(("TriLt", ["x", "y", "z"]), [("E", ["x", "y"]), ("E", ["y", "z"]), ("E", ["x", "z"]),
+                                           ("<", "x", "y"), ("<", "y", "z")], ["x", "y", "z"])]
+    unreach = P.TC + [(("V", ["x"]), [("E", ["x", "y"])], ["x", "y"]),
+                      (("NR", ["x", "y"]), [("V", ["x"]), ("V", ["y"]), ("not", ("Reach", ["x", "y"])),
+                                            ("!=", "x", "y")], ["x", "y"])]
+    cases = [({"E": 2, "TriLt": 3}, {"E": dg.rmat_edges(300, 2500, 5, symmetric=True)}, tri_lt),
+             ({"E": 2, "Reach": 2, "V": 1, "NR": 2}, {"E": dg.rmat_edges(200, 600, 6)}, unreach)]
+    with pkg.Server(budget_bytes=2 << 30, max_slots=2) as srv:
+        tickets = [srv.submit(rels, facts, rules) for rels, facts, rules in cases]
+        for (rels, facts, rules), t in zip(cases, tickets):
+            assert srv.wait(t) == pkg.DL_OK
+            eng = srv.result(t)
+            ref = oracle.evaluate(rels, facts, rules)
+            for name in rels:
+                assert np.array_equal(eng.fetch(name), ref.relations[name]), name
+            srv.release(t)
