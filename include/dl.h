@@ -109,6 +109,14 @@ typedef struct dl_config {
                                  it exceeds this percentage of the body, and at the stratum's end.
                                  Joins read body and head as one relation.  0 = default (25),
                                  UINT32_MAX = flush only at the stratum's end */
+    uint64_t dense_bytes;     /* dense relation bitmaps: during a recursive stratum's rounds, a
+                                 relation whose column domains (largest value + 1 per column, over
+                                 its rows and all rows the rules can derive) multiply to at most
+                                 8 x this many bits gets one bit per possible row; a round's new
+                                 rows are then found by one test-and-set per derived row (paper
+                                 Section 4, Compute Delta), replacing the probe of the relation's
+                                 index and the deduplicating sort.  At most a quarter of the
+                                 budget left.  0 = default (8 GiB), 1 = never */
     const char* tune_cache;   /* DL_FLAG_AUTOTUNE: text file of tuned choices, read when the
                                  engine is created (if it exists) and rewritten when it is
                                  destroyed or by dl_tune_save; NULL = choices kept in memory */
@@ -324,6 +332,7 @@ typedef struct dl_stats {
     uint32_t tuned_levels;     /* DL_FLAG_AUTOTUNE: join levels tuned by this call (new buckets) */
     uint32_t tune_hits;        /* DL_FLAG_AUTOTUNE: join levels that used a cached choice */
     uint32_t head_flushes;     /* heads merged into their bodies (dl_config.head_percent) */
+    uint32_t dense_relations;  /* relations given a dense bitmap for their rounds (dl_config.dense_bytes) */
 } dl_stats;
 
 /* Evaluate all rules to the least fixpoint (semi-naive, Jacobi rounds: every rule of a

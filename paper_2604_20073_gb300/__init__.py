@@ -50,7 +50,8 @@ class dl_config(ctypes.Structure):
                 ("alloc", DL_ALLOC_FN), ("free", DL_FREE_FN), ("alloc_user", ctypes.c_void_p),
                 ("flags", ctypes.c_uint32), ("tile_units", ctypes.c_uint32), ("instances", ctypes.c_uint32),
                 ("chunk_rows", ctypes.c_uint64), ("hub_rows", ctypes.c_uint32),
-                ("frontier_bytes", ctypes.c_uint64), ("head_percent", ctypes.c_uint32), ("tune_cache", ctypes.c_char_p)]
+                ("frontier_bytes", ctypes.c_uint64), ("head_percent", ctypes.c_uint32),
+                ("dense_bytes", ctypes.c_uint64), ("tune_cache", ctypes.c_char_p)]
 
 
 class dl_term(ctypes.Structure):
@@ -80,7 +81,7 @@ class dl_stats(ctypes.Structure):
                 ("kernels", dl_kernel_stat * len(KERNEL_KINDS)), ("top_kind", ctypes.c_uint32),
                 ("top", dl_kernel_stat), ("hub_keys", ctypes.c_uint32),
                 ("join_slices", ctypes.c_uint32), ("tuned_levels", ctypes.c_uint32), ("tune_hits", ctypes.c_uint32),
-                ("head_flushes", ctypes.c_uint32)]
+                ("head_flushes", ctypes.c_uint32), ("dense_relations", ctypes.c_uint32)]
 
 
 class dl_server_config(ctypes.Structure):
@@ -273,7 +274,8 @@ class Engine:
 
     def __init__(self, device: int = 0, stream=None, arena_bytes: int = 0, flags: int = 0, tile_units: int = 0,
                  use_torch_allocator: bool = False, instances: int = 0, chunk_rows: int = 0, hub_rows: int = 0,
-                 frontier_bytes: int = 0, tune_cache: str | None = None, head_percent: int = 0):
+                 frontier_bytes: int = 0, tune_cache: str | None = None, head_percent: int = 0,
+                 dense_bytes: int = 0):
         import torch  # plumbing only: stream handle and (optionally) the caching allocator
         self.lib = load_library()
         if not torch.cuda.is_available():
@@ -293,6 +295,7 @@ class Engine:
         cfg.hub_rows = hub_rows
         cfg.frontier_bytes = frontier_bytes
         cfg.head_percent = head_percent
+        cfg.dense_bytes = dense_bytes
         self._tune_cache = tune_cache.encode() if tune_cache else None   # kept alive for the engine
         cfg.tune_cache = self._tune_cache
         self.instances = instances

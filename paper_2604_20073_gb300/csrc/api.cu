@@ -1,6 +1,7 @@
 // C ABI entry points and the host runtime: relation store, stratification, semi-naive
 // rounds (paper Sections 2 and 4), fetch.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -565,10 +566,87 @@ Index sort_unique_index(Engine& E, DevPtr buf, TableView t, const Perm& perm, ui
     return compute_delta(E, sorted, empty_index(arity, perm), perm, arity, false);
 }
 
+// Rows of a raw table that are new to a relation in dense-bitmap form (each row's bit is
+// tested and set, so the kept rows are distinct and absent from the relation), as a sorted
+// index; `sorted` input stays sorted without a sort.
+Index dense_reduce(Engine& E, Relation& R, const TableView& t, bool sorted) {
+    Index o = make_index(E, R.arity, identity_perm(), t.n);
+    E.phase_begin(2);
+    o.n = dense_filter(E, t, R.dense_dom, (uint32_t*)R.dense->ptr, table_of(o));
+    E.phase_end(2);
+    if (sorted || o.n <= 1) return o;
+    TableView ot = table_of(o);
+    return sort_into_index(E, o.cols, ot, identity_perm(), R.arity, o.cap);
+}
+
 Index reduce_part(Engine& E, Relation& R, DevPtr buf, TableView t) {
+    if (R.dense) return dense_reduce(E, R, t, false);
     uint64_t stride = 0;
     auto f = prefilter(E, R, buf, t, stride);
     return sort_unique_index(E, f.first, f.second, identity_perm(), R.arity, stride);
+}
+
+// Largest value + 1 of every column of every relation, over its rows and every row the rules
+// can derive: a head column's values come from the body columns its variable is bound by, so
+// they are below the smallest of those bounds (a fixpoint over the rules; constants count).
+std::vector<std::array<uint32_t, kMaxArity>> column_domains(Engine& E) {
+    std::vector<std::array<uint32_t, kMaxArity>> dom(E.rels.size());
+    auto m = E.array<uint32_t>(kMaxArity);
+    for (size_t r = 0; r < E.rels.size(); r++) {
+        dom[r].fill(0);
+        const Relation& R = E.rels[r];
+        if (R.sink == DL_SINK_COUNT || R.full.empty() || R.full[0].n == 0) continue;
+        DL_CUDA(cudaMemsetAsync(m.p, 0, sizeof(uint32_t) * kMaxArity, E.stream));
+        for (uint32_t c = 0; c < R.arity; c++) column_max(E, R.full[0].col((int)c), R.full[0].n, m.p + c);
+        uint32_t mx[kMaxArity];
+        memcpy(mx, E.readback(m.p, kMaxArity / 2), sizeof(mx));
+        for (uint32_t c = 0; c < R.arity; c++) dom[r][c] = mx[c] + 1;
+    }
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (const Rule& q : E.rules) {
+            for (uint32_t c = 0; c < q.head.arity; c++) {
+                const dl_term& t = q.head.terms[c];
+                uint32_t bound = 0;
+                if (t.kind == DL_TERM_CONST) {
+                    bound = t.id + 1;
+                } else {
+                    bound = UINT32_MAX;
+                    for (const RuleAtom& a : q.body)
+                        for (uint32_t k = 0; k < a.arity; k++)
+                            if (a.terms[k].kind == DL_TERM_VAR && a.terms[k].id == t.id)
+                                bound = std::min(bound, dom[a.rel][k]);
+                    if (bound == UINT32_MAX) bound = E.V;
+                }
+                if (bound > dom[q.head.rel][c]) {
+                    dom[q.head.rel][c] = bound;
+                    changed = true;
+                }
+            }
+        }
+    }
+    return dom;
+}
+
+// Gives a stratum's relations their dense bitmaps where the domain product is small enough.
+void dense_begin(Engine& E, const Stratum& S) {
+    if (E.dense_bytes <= 1) return;
+    const auto dom = column_domains(E);
+    for (uint32_t r : S.rels) {
+        Relation& R = E.rels[r];
+        R.dense.reset();
+        if (R.sink == DL_SINK_COUNT) continue;
+        long double bits = 1;
+        for (uint32_t c = 0; c < R.arity; c++) bits *= (long double)std::max<uint32_t>(dom[r][c], 1);
+        const uint64_t room = E.budget > E.used ? (E.budget - E.used) / 4 : 0;
+        if (bits / 8 > (long double)std::min(E.dense_bytes, room)) continue;
+        const uint64_t words = ((uint64_t)bits + 31) / 32;
+        R.dense = E.make(sizeof(uint32_t) * words);
+        DL_CUDA(cudaMemsetAsync(R.dense->ptr, 0, sizeof(uint32_t) * words, E.stream));
+        for (uint32_t c = 0; c < kMaxArity; c++) R.dense_dom[c] = c < R.arity ? std::max<uint32_t>(dom[r][c], 1) : 1;
+        dense_set_rows(E, table_of(R.full[0]), R.dense_dom, (uint32_t*)R.dense->ptr);
+        E.dense_relations++;
+    }
 }
 
 // Turn one round's join outputs for relation R into its new delta; merge into full.
@@ -590,6 +668,9 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
         for (Index& rp : jo.rparts) acc = union_sorted(E, acc, rp);
         jo.rparts.clear();
         d = acc;
+    } else if (jo.parts.size() == 1 && jo.sorted_unique && R.dense) {
+        d = dense_reduce(E, R, jo.parts[0], true);   // sorted and distinct already: no sort
+        filtered = true;
     } else if (jo.parts.size() == 1 && jo.sorted_unique) {
         newrows.n = jo.parts[0].n;
         newrows.cap = newrows.n;
@@ -614,9 +695,13 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
         }
         jo.parts.clear();
         jo.owners.clear();
-        uint64_t stride = 0;
-        auto f = prefilter(E, R, buf, t, stride);
-        d = sort_unique_index(E, f.first, f.second, identity_perm(), R.arity, stride);
+        if (R.dense) {
+            d = dense_reduce(E, R, t, false);
+        } else {
+            uint64_t stride = 0;
+            auto f = prefilter(E, R, buf, t, stride);
+            d = sort_unique_index(E, f.first, f.second, identity_perm(), R.arity, stride);
+        }
         filtered = true;
     }
     if (!d.cols && d.n == 0) {
@@ -748,7 +833,7 @@ void fixpoint(Engine& E, dl_stats* st) {
     auto t0 = std::chrono::steady_clock::now();
     const uint64_t launches0 = E.launches;
     const uint64_t hub0 = E.hub_keys, slices0 = E.join_slices;
-    const uint64_t tuned0 = E.tuned_levels, hits0 = E.tune_hits, flush0 = E.head_flushes;
+    const uint64_t tuned0 = E.tuned_levels, hits0 = E.tune_hits, flush0 = E.head_flushes, dense0 = E.dense_relations;
     E.join_rows = E.count_rows = E.delta_rows = 0;
     E.peak = E.used;
     E.event_next = 0;
@@ -825,7 +910,9 @@ void fixpoint(Engine& E, dl_stats* st) {
         }
         uint32_t t = 1;
         if (!rec.empty() && any) {
-            // the stratum's relations take the head/body form for the rounds
+            // the stratum's relations take the head/body form (and, where their column domains
+            // are small, a dense bitmap) for the rounds
+            dense_begin(E, S);
             for (uint32_t r : S.rels) {
                 Relation& R = E.rels[r];
                 if (R.sink == DL_SINK_COUNT) continue;
@@ -855,12 +942,14 @@ void fixpoint(Engine& E, dl_stats* st) {
                     } catch (...) {
                     }
                     E.rels[r].head.clear();
+                    E.rels[r].dense.reset();
                 }
                 throw;
             }
             for (uint32_t r : S.rels) {
                 flush_head(E, E.rels[r]);
                 E.rels[r].head.clear();
+                E.rels[r].dense.reset();
             }
         }
         S.rounds = t;
@@ -900,6 +989,7 @@ void fixpoint(Engine& E, dl_stats* st) {
         st->tuned_levels = (uint32_t)(E.tuned_levels - tuned0);
         st->tune_hits = (uint32_t)(E.tune_hits - hits0);
         st->head_flushes = (uint32_t)(E.head_flushes - flush0);
+        st->dense_relations = (uint32_t)(E.dense_relations - dense0);
         double* ms[4] = {&st->ms_join, &st->ms_sort, &st->ms_dedup, &st->ms_merge};
         for (int k = 0; k < 4; k++)
             for (auto& pr : E.phases.ev[k]) {
@@ -1006,6 +1096,7 @@ int dl_engine_create(const dl_config* cfg, dl_engine** out) {
         if (c.chunk_rows) E->chunk_rows = c.chunk_rows;
         if (c.hub_rows) E->hub_rows = c.hub_rows;
         if (c.head_percent) E->head_percent = c.head_percent;
+        if (c.dense_bytes) E->dense_bytes = c.dense_bytes;
         E->frontier_bytes = c.frontier_bytes;
         if (c.tune_cache) {
             E->tune_path = c.tune_cache;

@@ -178,6 +178,13 @@ bool sort_unique_packed(Engine& E, const TableView& t, const std::function<Table
 // allow_pack: rows whose varying bits fit in 64 bits are sorted as packed keys.
 void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out, bool allow_pack = true);
 
+// Dense relation bitmaps (column c of the relation below dom[c]; bit index in mixed radix,
+// column 0 most significant).  dense_set_rows sets the rows' bits; dense_filter keeps, in
+// input order, the rows whose bit was clear and sets it (so the kept rows are distinct and
+// new), returning their count (synchronises).  A row outside the domain is DL_ERR_STATE.
+void dense_set_rows(Engine& E, const TableView& t, const uint32_t* dom, uint32_t* bits);
+uint64_t dense_filter(Engine& E, const TableView& in, const uint32_t* dom, uint32_t* bits, const TableView& out);
+
 // Keep rows that differ from their predecessor and (if full.n > 0) are absent from full.
 // in is sorted; writes the kept rows, in order, to out; returns the count (synchronises).
 uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const TableView& out);

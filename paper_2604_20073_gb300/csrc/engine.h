@@ -32,6 +32,10 @@ struct Relation {
     // rows added since the last flush; the relation is their (disjoint) union.  Empty outside
     // the rounds: the stratum's end flushes every head into its body.
     std::vector<Index> head;
+    // Dense bitmap of the relation's rows during a recursive stratum's rounds (when its column
+    // domains are small enough): the round's delta is found by one test-and-set per raw row.
+    DevPtr dense;
+    uint32_t dense_dom[kMaxArity] = {0};
     bool full_perms_built = false;    // full[k > 0] are up to date
     std::vector<bool> root_needed;    // per perm: build dense root offsets
     uint64_t sink_count = 0;
@@ -111,6 +115,8 @@ class Engine {
     uint64_t frontier_bytes = 0;      // join frontier bytes before slicing (0: a third of the budget left)
     uint64_t join_slices = 0;         // levels whose input was processed in slices
     uint32_t head_percent = 25;       // flush a head into its body above this percentage of the body
+    uint64_t dense_bytes = 8ull << 30;  // largest dense relation bitmap (and at most a quarter of the budget left)
+    uint64_t dense_relations = 0;
     uint64_t head_flushes = 0;
     std::map<std::string, TuneChoice> tune;   // DL_FLAG_AUTOTUNE: choices by rule, level and size bucket
     std::string tune_path;            // file the choices are loaded from and saved to ("" = none)

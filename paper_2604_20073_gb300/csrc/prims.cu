@@ -431,6 +431,78 @@ __global__ void k_key_distinct_write(const uint32_t* __restrict__ khi, const uin
     }
 }
 
+// Dense relation bitmaps: bit v0 * d1 * d2 ... + v1 * d2 ... + v(a-1) of a relation whose column c
+// holds values below dom.d[c].
+struct DenseDom {
+    uint32_t arity;
+    uint32_t d[kMaxArity];
+};
+
+__device__ __forceinline__ uint64_t dense_index(const TableView& t, uint64_t i, const DenseDom& D, bool& ok) {
+    uint64_t idx = 0;
+    for (uint32_t c = 0; c < D.arity; c++) {
+        const uint32_t v = t.col[c][i];
+        ok = ok && v < D.d[c];
+        idx = idx * D.d[c] + v;
+    }
+    return idx;
+}
+
+__global__ void k_dense_set(const __grid_constant__ TableView t, const __grid_constant__ DenseDom D,
+                            uint32_t* __restrict__ bits, unsigned long long* __restrict__ bad) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < t.n; i += (uint64_t)gridDim.x * blockDim.x) {
+        bool ok = true;
+        const uint64_t idx = dense_index(t, i, D, ok);
+        if (!ok) {
+            atomicAdd(bad, 1ull);
+            continue;
+        }
+        atomicOr(bits + (idx >> 5), 1u << (idx & 31));
+    }
+}
+
+// Test-and-set every row's bit: a row is new iff its bit was clear (it is neither in the
+// relation nor earlier in this input).  flags[i] = 1 for new rows; per-tile counts.
+__global__ void k_dense_flags(const __grid_constant__ TableView t, const __grid_constant__ DenseDom D,
+                              uint32_t* __restrict__ bits, uint8_t* __restrict__ flags,
+                              uint64_t* __restrict__ block_count, unsigned long long* __restrict__ bad) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    uint64_t c = 0;
+    for (int j = 0; j < kCompItems; j++) {
+        const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+        if (i >= t.n) continue;
+        bool ok = true;
+        const uint64_t idx = dense_index(t, i, D, ok);
+        uint8_t f = 0;
+        if (!ok) {
+            atomicAdd(bad, 1ull);
+        } else {
+            const uint32_t m = 1u << (idx & 31);
+            f = (atomicOr(bits + (idx >> 5), m) & m) ? 0 : 1;
+        }
+        flags[i] = f;
+        c += f;
+    }
+    uint64_t total;
+    block_exclusive_scan(c, total);
+    if (threadIdx.x == 0) block_count[blockIdx.x] = total;
+}
+
+__global__ void k_dense_write(const __grid_constant__ TableView in, const uint8_t* __restrict__ flags,
+                              const __grid_constant__ TableView out, const uint64_t* __restrict__ block_off) {
+    const uint64_t base = (uint64_t)blockIdx.x * kCompTile;
+    uint64_t run = block_off[blockIdx.x];
+    for (int j = 0; j < kCompItems; j++) {
+        const uint64_t i = base + (uint64_t)j * blockDim.x + threadIdx.x;
+        const uint32_t f = i < in.n ? flags[i] : 0u;
+        uint32_t total;
+        const uint32_t pos = block_exclusive_scan(f, total);
+        if (f)
+            for (uint32_t c = 0; c < in.arity; c++) out.col[c][run + pos] = in.col[c][i];
+        run += total;
+    }
+}
+
 // ------------------------------------------------------------------ merge
 
 constexpr int kMergeThreads = 256;
@@ -774,6 +846,51 @@ bool sort_unique_packed(Engine& E, const TableView& t, const std::function<Table
         DL_CHECK_LAUNCH();
     }
     return true;
+}
+
+void dense_set_rows(Engine& E, const TableView& t, const uint32_t* dom, uint32_t* bits) {
+    if (!t.n) return;
+    DenseDom D;
+    memset(&D, 0, sizeof(D));
+    D.arity = t.arity;
+    for (uint32_t c = 0; c < t.arity; c++) D.d[c] = dom[c];
+    auto bad = E.array<uint64_t>(1);
+    DL_CUDA(cudaMemsetAsync(bad.p, 0, 8, E.stream));
+    {
+        KernelScope ks(E, DL_K_DELTA, 4ull * t.arity * t.n);
+        k_dense_set<<<grid_for(t.n, 256), 256, 0, E.stream>>>(t, D, bits, (unsigned long long*)bad.p);
+        DL_CHECK_LAUNCH();
+    }
+    if (E.readback(bad.p, 1)[0]) throw Error(DL_ERR_STATE, "a row lies outside its relation's dense domain");
+}
+
+uint64_t dense_filter(Engine& E, const TableView& in, const uint32_t* dom, uint32_t* bits, const TableView& out) {
+    const uint64_t n = in.n;
+    if (n == 0) return 0;
+    DenseDom D;
+    memset(&D, 0, sizeof(D));
+    D.arity = in.arity;
+    for (uint32_t c = 0; c < in.arity; c++) D.d[c] = dom[c];
+    const uint64_t nb = (n + kCompTile - 1) / kCompTile;
+    auto cnt = E.array<uint64_t>(nb + 2);
+    auto flags = E.array<uint8_t>(n);
+    DL_CUDA(cudaMemsetAsync(cnt.p + nb + 1, 0, 8, E.stream));
+    {
+        KernelScope ks(E, DL_K_DELTA, 4ull * in.arity * n);
+        k_dense_flags<<<(unsigned)nb, kCompThreads, 0, E.stream>>>(in, D, bits, flags.p, cnt.p,
+                                                                  (unsigned long long*)(cnt.p + nb + 1));
+        DL_CHECK_LAUNCH();
+    }
+    scan_u64(E, cnt.p, nb, false, cnt.p + nb);
+    const uint64_t* h = E.readback(cnt.p + nb, 2);
+    const uint64_t total = h[0];
+    if (h[1]) throw Error(DL_ERR_STATE, "a row lies outside its relation's dense domain");
+    if (total) {
+        KernelScope ks(E, DL_K_DELTA, (4ull * in.arity + 1) * n + 4ull * in.arity * total);
+        k_dense_write<<<(unsigned)nb, kCompThreads, 0, E.stream>>>(in, flags.p, out, cnt.p);
+        DL_CHECK_LAUNCH();
+    }
+    return total;
 }
 
 uint64_t unique_anti(Engine& E, const TableView& in, const AtomView* full, const TableView& out) {
