@@ -566,8 +566,12 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
         EntryState<NS> S;
         uint32_t r = 0;
         uint64_t hpre = 0;        // MODE_COUNT: row hash over the head columns before head_lvl
-        uint64_t hsh = 0;         // hash of the columns shared by the current sibling run
-        uint32_t run = 0xFFFFFFFFu;
+        // hash of the columns shared by the current sibling run, and that run (warp-uniform,
+        // kept in shared memory: registers are the limit here)
+        __shared__ unsigned long long s_hsh[kWarps];
+        __shared__ uint32_t s_run[kWarps];
+        if (lane == 0) s_run[threadIdx.x >> 5] = 0xFFFFFFFFu;
+        __syncwarp();
         for (;;) {
             const uint64_t wlo = s_wlo[threadIdx.x >> 5], whi = s_whi[threadIdx.x >> 5];
             const uint32_t stop = (uint32_t)(min(entry_load(P, S, e, wlo), whi) - wlo);
@@ -575,13 +579,18 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
                 int c0 = 0;
                 if (P.head_shared > 0) {
                     const uint32_t g = __ldg(P.seg + e);
-                    if (g != run) {
-                        run = g;
-                        hsh = kTupleHashSeed;
+                    if (g != s_run[threadIdx.x >> 5]) {
+                        uint64_t hsh = kTupleHashSeed;
                         for (int c = 0; c < P.head_shared; c++) hsh = tuple_hash_step(hsh, head_value(P, c, e), c);
+                        __syncwarp();
+                        if (lane == 0) {
+                            s_run[threadIdx.x >> 5] = g;
+                            s_hsh[threadIdx.x >> 5] = hsh;
+                        }
+                        __syncwarp();
                     }
                     c0 = P.head_shared;
-                    hpre = hsh;
+                    hpre = s_hsh[threadIdx.x >> 5];
                 } else {
                     hpre = kTupleHashSeed;
                 }
