@@ -569,7 +569,7 @@ int dl_tune_save(dl_engine* e, const char* path);
  * Limits: arity 1..DL_NOALLOC_MAX_ARITY, nrows <= DL_NOALLOC_MAX_ROWS; larger inputs are
  * rejected with DL_ERR_CAPACITY before any work is issued.
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture begins.
+ * (cudaGetSymbolAddress) and keeps it for later calls.
  * Sharing: all calls on a device use the same array, which keeps the previous call's
  * contents (every counter the call reads is rewritten by the call first).  Calls whose
  * work overlaps on the GPU -- on different streams or threads without ordering between

@@ -462,7 +462,9 @@ __global__ void k_dense_set(const __grid_constant__ TableView t, const __grid_co
 }
 
 // Test-and-set every row's bit: a row is new iff its bit was clear (it is neither in the
-// relation nor earlier in this input).  flags[i] = 1 for new rows; per-tile counts.
+// relation nor earlier in this input).  flags[i] = 1 for new rows; per-tile counts.  Bits only
+// go from 0 to 1 here, so a set bit read from L2 settles the row without the atomic; most
+// rows of a projecting rule are duplicates, and a plain load costs far less than an atomic.
 __global__ void k_dense_flags(const __grid_constant__ TableView t, const __grid_constant__ DenseDom D,
                               uint32_t* __restrict__ bits, uint8_t* __restrict__ flags,
                               uint64_t* __restrict__ block_count, unsigned long long* __restrict__ bad) {
@@ -478,7 +480,8 @@ __global__ void k_dense_flags(const __grid_constant__ TableView t, const __grid_
             atomicAdd(bad, 1ull);
         } else {
             const uint32_t m = 1u << (idx & 31);
-            f = (atomicOr(bits + (idx >> 5), m) & m) ? 0 : 1;
+            uint32_t* w = bits + (idx >> 5);
+            f = (__ldcg(w) & m) ? 0 : (atomicOr(w, m) & m) ? 0 : 1;
         }
         flags[i] = f;
         c += f;
