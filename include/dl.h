@@ -63,6 +63,12 @@ extern "C" {
                                      every later run of that bucket (dl_config.tune_cache keeps the
                                      choices across engines); ignored when dl_config.tile_units is
                                      set.  Results never depend on the choice */
+#define DL_FLAG_NO_DENSE_SINK 0x10u /* A/B baseline: rules deriving a relation that has a dense
+                                     bitmap (dl_config.dense_bytes) write their rows out, which are
+                                     then test-and-set and compacted, instead of the join's last
+                                     level test-and-setting them in the bitmap directly (the dense
+                                     sink, whose round delta is read back from the bits set since
+                                     the previous round).  Results never depend on it */
 
 typedef struct dl_engine dl_engine;
 typedef uint32_t dl_rel_id;

@@ -32,6 +32,7 @@ DL_FLAG_NAIVE_ROOTS = 0x1
 DL_FLAG_DEBUG_CHECKS = 0x2
 DL_FLAG_PROFILE = 0x4
 DL_FLAG_AUTOTUNE = 0x8
+DL_FLAG_NO_DENSE_SINK = 0x10
 KERNEL_KINDS = ["join_hist", "join_count", "join_write", "scan", "sort", "delta", "merge", "other"]
 DL_SINK_STORE, DL_SINK_COUNT = 0, 1
 DL_TERM_VAR, DL_TERM_CONST = 0, 1

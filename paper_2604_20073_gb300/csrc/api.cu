@@ -579,7 +579,32 @@ Index dense_reduce(Engine& E, Relation& R, const TableView& t, bool sorted) {
     return sort_into_index(E, o.cols, ot, identity_perm(), R.arity, o.cap);
 }
 
+// Rows of a raw table set in a relation's dense bitmap (dense sink: the round's end extracts
+// every row set since the last extraction, sorted and distinct).
+void dense_mark(Engine& E, Relation& R, const TableView& t) {
+    E.phase_begin(2);
+    dense_set_rows(E, t, R.dense_dom, (uint32_t*)R.dense->ptr, (uint8_t*)R.dense_dirty->ptr);
+    E.phase_end(2);
+}
+
+// The rows set in a relation's dense bitmap since the last extraction, as a sorted index.
+Index dense_take(Engine& E, Relation& R) {
+    Index o;
+    E.phase_begin(2);
+    o.n = dense_extract(E, R.arity, R.dense_dom, (const uint32_t*)R.dense->ptr, (uint32_t*)R.dense_old->ptr,
+                        (uint8_t*)R.dense_dirty->ptr, R.dense_words, [&](uint64_t m) {
+                            o = make_index(E, R.arity, identity_perm(), m);
+                            return table_of(o);
+                        });
+    E.phase_end(2);
+    return o;
+}
+
 Index reduce_part(Engine& E, Relation& R, DevPtr buf, TableView t) {
+    if (R.dense && R.dense_dirty) {
+        dense_mark(E, R, t);
+        return empty_index(R.arity, identity_perm());
+    }
     if (R.dense) return dense_reduce(E, R, t, false);
     uint64_t stride = 0;
     auto f = prefilter(E, R, buf, t, stride);
@@ -628,23 +653,41 @@ std::vector<std::array<uint32_t, kMaxArity>> column_domains(Engine& E) {
     return dom;
 }
 
+void dense_end(Relation& R) {
+    R.dense.reset();
+    R.dense_old.reset();
+    R.dense_dirty.reset();
+    R.dense_words = 0;
+}
+
 // Gives a stratum's relations their dense bitmaps where the domain product is small enough.
 void dense_begin(Engine& E, const Stratum& S) {
     if (E.dense_bytes <= 1) return;
     const auto dom = column_domains(E);
+    const bool sink = !(E.flags & DL_FLAG_NO_DENSE_SINK);
     for (uint32_t r : S.rels) {
         Relation& R = E.rels[r];
-        R.dense.reset();
+        dense_end(R);
         if (R.sink == DL_SINK_COUNT) continue;
         long double bits = 1;
         for (uint32_t c = 0; c < R.arity; c++) bits *= (long double)std::max<uint32_t>(dom[r][c], 1);
-        const uint64_t room = E.budget > E.used ? (E.budget - E.used) / 4 : 0;
+        // the dense sink keeps a second copy (the bitmap as of the last extraction)
+        const uint64_t room = E.budget > E.used ? (E.budget - E.used) / (sink ? 8 : 4) : 0;
         if (bits / 8 > (long double)std::min(E.dense_bytes, room)) continue;
         const uint64_t words = ((uint64_t)bits + 31) / 32;
         R.dense = E.make(sizeof(uint32_t) * words);
+        R.dense_words = words;
         DL_CUDA(cudaMemsetAsync(R.dense->ptr, 0, sizeof(uint32_t) * words, E.stream));
         for (uint32_t c = 0; c < kMaxArity; c++) R.dense_dom[c] = c < R.arity ? std::max<uint32_t>(dom[r][c], 1) : 1;
         dense_set_rows(E, table_of(R.full[0]), R.dense_dom, (uint32_t*)R.dense->ptr);
+        if (sink) {
+            const uint64_t blocks = (words + kDenseBlockWords - 1) / kDenseBlockWords;
+            R.dense_old = E.make(sizeof(uint32_t) * words);
+            R.dense_dirty = E.make(blocks);
+            DL_CUDA(cudaMemcpyAsync(R.dense_old->ptr, R.dense->ptr, sizeof(uint32_t) * words, cudaMemcpyDeviceToDevice,
+                                    E.stream));
+            DL_CUDA(cudaMemsetAsync(R.dense_dirty->ptr, 0, blocks, E.stream));
+        }
         E.dense_relations++;
     }
 }
@@ -659,7 +702,17 @@ uint64_t absorb_round(Engine& E, Relation& R, PendingOut& P, bool keep_delta) {
     uint64_t raw = 0;
     for (auto& p : jo.parts) raw += p.n;
     Index d;
-    if (!jo.rparts.empty() || raw > E.chunk_rows) {
+    if (R.dense && R.dense_dirty) {
+        // dense sink: the joins set their rows' bits; raw parts of other variants are set too,
+        // and the round's delta is every bit set since the last extraction (sorted, distinct,
+        // absent from the relation)
+        for (auto& p : jo.parts) dense_mark(E, R, p);
+        jo.parts.clear();
+        jo.owners.clear();
+        jo.rparts.clear();
+        d = dense_take(E, R);
+        filtered = true;
+    } else if (!jo.rparts.empty() || raw > E.chunk_rows) {
         // reduce every part on its own, then union (memory stays proportional to new tuples)
         Index acc = empty_index(R.arity, identity_perm());
         for (size_t i = 0; i < jo.parts.size(); i++) acc = union_sorted(E, acc, reduce_part(E, R, jo.owners[i], jo.parts[i]));
@@ -942,14 +995,14 @@ void fixpoint(Engine& E, dl_stats* st) {
                     } catch (...) {
                     }
                     E.rels[r].head.clear();
-                    E.rels[r].dense.reset();
+                    dense_end(E.rels[r]);
                 }
                 throw;
             }
             for (uint32_t r : S.rels) {
                 flush_head(E, E.rels[r]);
                 E.rels[r].head.clear();
-                E.rels[r].dense.reset();
+                dense_end(E.rels[r]);
             }
         }
         S.rounds = t;

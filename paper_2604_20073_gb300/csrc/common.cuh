@@ -19,6 +19,8 @@ constexpr int kMaxVars = DL_MAX_VARS;
 constexpr int kMaxAtoms = DL_MAX_BODY;
 constexpr int kMaxSrc = 8;   // atoms that mention one variable (sources of one join level)
 constexpr uint32_t kDenseRootLimit = 1u << 27;  // dense root offsets only below this domain size
+constexpr int kDenseBlockShift = 8;              // dense relation bitmaps: 2^8 words per dirty block
+constexpr uint64_t kDenseBlockWords = 1ull << kDenseBlockShift;
 
 // ---------------------------------------------------------------- errors
 
@@ -182,8 +184,15 @@ void radix_sort_rows(Engine& E, TableView& t, TableView& tmp, int* passes_out, b
 // column 0 most significant).  dense_set_rows sets the rows' bits; dense_filter keeps, in
 // input order, the rows whose bit was clear and sets it (so the kept rows are distinct and
 // new), returning their count (synchronises).  A row outside the domain is DL_ERR_STATE.
-void dense_set_rows(Engine& E, const TableView& t, const uint32_t* dom, uint32_t* bits);
+// With `dirty` (one byte per kDenseBlockWords words), every bit that goes from 0 to 1 marks
+// its block, and dense_extract later lists the bits set since the last extraction.
+void dense_set_rows(Engine& E, const TableView& t, const uint32_t* dom, uint32_t* bits, uint8_t* dirty = nullptr);
 uint64_t dense_filter(Engine& E, const TableView& in, const uint32_t* dom, uint32_t* bits, const TableView& out);
+// Rows whose bits are set in `bits` but not in `old`, looked for in the blocks marked dirty:
+// written in bit order (sorted lexicographically, distinct) to the table alloc_out(count)
+// returns; then old = bits and dirty = 0 in those blocks.  Returns the count (synchronises).
+uint64_t dense_extract(Engine& E, uint32_t arity, const uint32_t* dom, const uint32_t* bits, uint32_t* old,
+                       uint8_t* dirty, uint64_t nwords, const std::function<TableView(uint64_t)>& alloc_out);
 
 // Keep rows that differ from their predecessor and (if full.n > 0) are absent from full.
 // in is sorted; writes the kept rows, in order, to out; returns the count (synchronises).

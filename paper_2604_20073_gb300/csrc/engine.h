@@ -36,6 +36,11 @@ struct Relation {
     // domains are small enough): the round's delta is found by one test-and-set per raw row.
     DevPtr dense;
     uint32_t dense_dom[kMaxArity] = {0};
+    // Dense sink (rule rows test-and-set straight into `dense` by the join): the bitmap as of
+    // the last extraction, and one byte per kDenseBlockWords words marking blocks with bits set
+    // since then.  Null when the rows are materialised and filtered instead.
+    DevPtr dense_old, dense_dirty;
+    uint64_t dense_words = 0;
     bool full_perms_built = false;    // full[k > 0] are up to date
     std::vector<bool> root_needed;    // per perm: build dense root offsets
     uint64_t sink_count = 0;
@@ -189,6 +194,8 @@ struct JoinOutput {
     std::vector<DevPtr> owners;
     std::vector<Index> rparts;        // parts already sorted, deduplicated and anti-joined with full
     bool sorted_unique = true;        // a single unreduced part is sorted (canonical) and distinct
+    bool dense_sunk = false;          // rows went to the head's dense bitmap (extracted at the round's end)
+    uint64_t dense_rows = 0;          // raw rows those were
     // Receives an output chunk of a rule whose output exceeds the chunk size; it reduces the
     // chunk and appends it as a reduced part.
     std::function<void(DevPtr, TableView)> chunk_sink;

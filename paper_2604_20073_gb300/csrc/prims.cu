@@ -449,7 +449,8 @@ __device__ __forceinline__ uint64_t dense_index(const TableView& t, uint64_t i, 
 }
 
 __global__ void k_dense_set(const __grid_constant__ TableView t, const __grid_constant__ DenseDom D,
-                            uint32_t* __restrict__ bits, unsigned long long* __restrict__ bad) {
+                            uint32_t* __restrict__ bits, uint8_t* __restrict__ dirty,
+                            unsigned long long* __restrict__ bad) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < t.n; i += (uint64_t)gridDim.x * blockDim.x) {
         bool ok = true;
         const uint64_t idx = dense_index(t, i, D, ok);
@@ -457,8 +458,78 @@ __global__ void k_dense_set(const __grid_constant__ TableView t, const __grid_co
             atomicAdd(bad, 1ull);
             continue;
         }
-        atomicOr(bits + (idx >> 5), 1u << (idx & 31));
+        uint32_t* w = bits + (idx >> 5);
+        const uint32_t m = 1u << (idx & 31);
+        if (__ldcg(w) & m) continue;   // set already (bits only go from 0 to 1 here)
+        if (!(atomicOr(w, m) & m) && dirty) dirty[idx >> (5 + kDenseBlockShift)] = 1;
     }
+}
+
+// Dense extraction, one warp per block of kDenseBlockWords words (8 per lane): the bits set in
+// `bits` but not in `old`.  Count pass: per block; clean blocks count 0.
+constexpr int kExtractWarps = 8;
+constexpr int kWordsPerLane = (int)(kDenseBlockWords / 32);
+
+__global__ void k_dense_block_count(const uint32_t* __restrict__ bits, const uint32_t* __restrict__ old,
+                                    const uint8_t* __restrict__ dirty, uint64_t nwords, uint64_t nblocks,
+                                    uint64_t* __restrict__ bcnt) {
+    const uint64_t b = blockIdx.x * (uint64_t)kExtractWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nblocks) return;
+    uint32_t c = 0;
+    if (dirty[b]) {
+        const uint64_t w0 = b * kDenseBlockWords + (uint64_t)lane * kWordsPerLane;
+#pragma unroll
+        for (int k = 0; k < kWordsPerLane; k++)
+            if (w0 + k < nwords) c += __popc(bits[w0 + k] & ~old[w0 + k]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) bcnt[b] = c;
+}
+
+// Write pass: each lane writes its words' new rows in bit order (its offset from an exclusive
+// warp scan of the lanes' counts), decoding the mixed-radix index into columns; then the
+// block's old words take the current bits and the block is clean again.
+__global__ void k_dense_block_write(const uint32_t* __restrict__ bits, uint32_t* __restrict__ old,
+                                    uint8_t* __restrict__ dirty, uint64_t nwords, uint64_t nblocks,
+                                    const uint64_t* __restrict__ boff, const __grid_constant__ DenseDom D,
+                                    const __grid_constant__ TableView out) {
+    const uint64_t b = blockIdx.x * (uint64_t)kExtractWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nblocks || !dirty[b]) return;
+    const uint64_t w0 = b * kDenseBlockWords + (uint64_t)lane * kWordsPerLane;
+    uint32_t nw[kWordsPerLane];
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kWordsPerLane; k++) {
+        nw[k] = w0 + k < nwords ? bits[w0 + k] & ~old[w0 + k] : 0u;
+        c += __popc(nw[k]);
+    }
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    uint64_t at = boff[b] + (incl - c);
+#pragma unroll
+    for (int k = 0; k < kWordsPerLane; k++) {
+        uint32_t m = nw[k];
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1;
+            uint64_t idx = (w0 + k) * 32 + (uint64_t)bit;
+            for (int col = (int)D.arity - 1; col >= 0; col--) {
+                out.col[col][at] = (uint32_t)(idx % D.d[col]);
+                idx /= D.d[col];
+            }
+            at++;
+        }
+        if (w0 + k < nwords) old[w0 + k] |= nw[k];
+    }
+    __syncwarp();
+    if (lane == 0) dirty[b] = 0;
 }
 
 // Test-and-set every row's bit: a row is new iff its bit was clear (it is neither in the
@@ -851,7 +922,7 @@ bool sort_unique_packed(Engine& E, const TableView& t, const std::function<Table
     return true;
 }
 
-void dense_set_rows(Engine& E, const TableView& t, const uint32_t* dom, uint32_t* bits) {
+void dense_set_rows(Engine& E, const TableView& t, const uint32_t* dom, uint32_t* bits, uint8_t* dirty) {
     if (!t.n) return;
     DenseDom D;
     memset(&D, 0, sizeof(D));
@@ -861,7 +932,7 @@ void dense_set_rows(Engine& E, const TableView& t, const uint32_t* dom, uint32_t
     DL_CUDA(cudaMemsetAsync(bad.p, 0, 8, E.stream));
     {
         KernelScope ks(E, DL_K_DELTA, 4ull * t.arity * t.n);
-        k_dense_set<<<grid_for(t.n, 256), 256, 0, E.stream>>>(t, D, bits, (unsigned long long*)bad.p);
+        k_dense_set<<<grid_for(t.n, 256), 256, 0, E.stream>>>(t, D, bits, dirty, (unsigned long long*)bad.p);
         DL_CHECK_LAUNCH();
     }
     if (E.readback(bad.p, 1)[0]) throw Error(DL_ERR_STATE, "a row lies outside its relation's dense domain");
@@ -891,6 +962,34 @@ uint64_t dense_filter(Engine& E, const TableView& in, const uint32_t* dom, uint3
     if (total) {
         KernelScope ks(E, DL_K_DELTA, (4ull * in.arity + 1) * n + 4ull * in.arity * total);
         k_dense_write<<<(unsigned)nb, kCompThreads, 0, E.stream>>>(in, flags.p, out, cnt.p);
+        DL_CHECK_LAUNCH();
+    }
+    return total;
+}
+
+uint64_t dense_extract(Engine& E, uint32_t arity, const uint32_t* dom, const uint32_t* bits, uint32_t* old,
+                       uint8_t* dirty, uint64_t nwords, const std::function<TableView(uint64_t)>& alloc_out) {
+    DenseDom D;
+    memset(&D, 0, sizeof(D));
+    D.arity = arity;
+    for (uint32_t c = 0; c < arity; c++) D.d[c] = dom[c];
+    const uint64_t nblocks = (nwords + kDenseBlockWords - 1) / kDenseBlockWords;
+    const uint64_t grid = (nblocks + kExtractWarps - 1) / kExtractWarps;
+    if (grid >= (1ull << 31)) throw Error(DL_ERR_CAPACITY, "dense bitmap too large to extract");
+    auto bcnt = E.array<uint64_t>(nblocks + 1);
+    {
+        KernelScope ks(E, DL_K_DELTA, nblocks);
+        k_dense_block_count<<<(unsigned)grid, 32 * kExtractWarps, 0, E.stream>>>(bits, old, dirty, nwords, nblocks,
+                                                                                 bcnt.p);
+        DL_CHECK_LAUNCH();
+    }
+    scan_u64(E, bcnt.p, nblocks, false, bcnt.p + nblocks);
+    const uint64_t total = E.readback(bcnt.p + nblocks, 1)[0];
+    const TableView out = alloc_out(total);
+    if (total) {
+        KernelScope ks(E, DL_K_DELTA, 4ull * arity * total);
+        k_dense_block_write<<<(unsigned)grid, 32 * kExtractWarps, 0, E.stream>>>(bits, old, dirty, nwords, nblocks,
+                                                                                 bcnt.p, D, out);
         DL_CHECK_LAUNCH();
     }
     return total;

@@ -274,9 +274,9 @@ __global__ void k_slice_cuts(const unsigned long long* __restrict__ bc, uint64_t
 }
 
 // Autotuner key: the rule's shape (relation names, terms, variable order), the level, and the
-// size bucket of its work (log2 of the units and of the frontier entries), its source count
-// and whether it filters.
-std::string tune_key(const Rule& R, uint32_t lvl, uint64_t T, uint64_t nF, uint32_t nsrc, bool filt) {
+// size bucket of its work (log2 of the units and of the frontier entries), its source count,
+// whether it filters, and whether its rows go to a dense bitmap (suffix ":D").
+std::string tune_key(const Rule& R, uint32_t lvl, uint64_t T, uint64_t nF, uint32_t nsrc, bool filt, int mode) {
     uint64_t h = 1469598103934665603ull;   // FNV-1a over the rule's structure
     auto mixin = [&](uint64_t v) {
         for (int k = 0; k < 8; k++) {
@@ -303,8 +303,8 @@ std::string tune_key(const Rule& R, uint32_t lvl, uint64_t T, uint64_t nF, uint3
     }
     auto lg = [](uint64_t x) { return x ? 63 - __builtin_clzll(x) : 0; };
     char buf[128];
-    snprintf(buf, sizeof(buf), "%016llx:L%u:T%d:F%d:S%u:f%d", (unsigned long long)h, lvl, lg(T), lg(nF), nsrc,
-             filt ? 1 : 0);
+    snprintf(buf, sizeof(buf), "%016llx:L%u:T%d:F%d:S%u:f%d%s", (unsigned long long)h, lvl, lg(T), lg(nF), nsrc,
+             filt ? 1 : 0, mode == MODE_DENSE ? ":D" : "");
     return buf;
 }
 
@@ -333,6 +333,7 @@ struct JoinRun {
     Plan plan;
     std::vector<LevelFilters> lf;
     bool count_sink = false;
+    bool dense_sink = false;   // the last level test-and-sets rows in the head's dense bitmap
     LevelParams base;
 
     JoinRun(Engine& e, const Rule& r, const std::vector<const Index*>& ns, Relation& h, JoinOutput& o)
@@ -469,9 +470,27 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
             while (P.head_shared < P.head_lvl && P.head_pos[P.head_shared] >= 0 &&
                    P.head_pos[P.head_shared] < (int)lvl - 1)
                 P.head_shared++;
+    } else if (last && dense_sink) {
+        // rows go straight into the head relation's dense bitmap: no write pass, no raw output
+        P.mode = MODE_DENSE;
+        P.dense_bits = (uint32_t*)head.dense->ptr;
+        P.dense_dirty = (uint8_t*)head.dense_dirty->ptr;
+        unsigned long long mul = 1;
+        P.dense_lvl_mul = 0;
+        P.dense_lvl_dom = UINT32_MAX;
+        for (int c = (int)P.head_arity - 1; c >= 0; c--) {
+            P.dense_mul[c] = mul;
+            P.dense_dom[c] = head.dense_dom[c];
+            if (P.head_pos[c] == (int)lvl) {
+                P.dense_lvl_mul += mul;
+                P.dense_lvl_dom = std::min(P.dense_lvl_dom, head.dense_dom[c]);
+            }
+            mul *= head.dense_dom[c];
+        }
     } else {
         P.mode = last ? MODE_HEAD : MODE_FRONTIER;
     }
+    const bool dmode = P.mode == MODE_DENSE;
     auto count_with = [&](uint32_t tile, bool wmk, bool timed) {
         CountRun r;
         r.tile = tile;
@@ -484,7 +503,7 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
         P.block_count = (unsigned long long*)r.bc.p;
         const bool per_inst = P.mode == MODE_COUNT && E.instances;   // batched count sink
         if (per_inst) wmk = r.wm = false;
-        if (P.mode == MODE_COUNT) {
+        if (P.mode == MODE_COUNT || dmode) {
             const uint64_t words = per_inst ? 3ull * E.instances : 3;
             r.dg = E.array<uint64_t>(words);
             DL_CUDA(cudaMemsetAsync(r.dg.p, 0, 8 * words, E.stream));
@@ -500,9 +519,11 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
             KernelScope ks(E, DL_K_JOIN_COUNT, 4 * Tmin + (entry_bytes + 9) * nF, 1, Tmin, nF);
             if (per_inst && filt) k_wcoj_count_inst<true><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
             else if (per_inst) k_wcoj_count_inst<false><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
-            else if (wmk) DL_NS_DISPATCH(k_wcoj_count_wm, P.nsrc, filt, (unsigned)r.ntiles, E.stream, P);
-            else if (filt) k_wcoj_count<true><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
-            else k_wcoj_count<false><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
+            else if (wmk) DL_NS_DISPATCH_D(k_wcoj_count_wm, P.nsrc, filt, dmode, (unsigned)r.ntiles, E.stream, P);
+            else if (filt && dmode) k_wcoj_count<true, true><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
+            else if (dmode) k_wcoj_count<false, true><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
+            else if (filt) k_wcoj_count<true, false><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
+            else k_wcoj_count<false, false><<<(unsigned)r.ntiles, kJoinThreads, 0, E.stream>>>(P);
             DL_CHECK_LAUNCH();
         }
         if (timed) {
@@ -518,7 +539,7 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
     CountRun cr;
     bool tuned = false;
     if ((E.flags & DL_FLAG_AUTOTUNE) && !P.naive && !E.tile_units) {
-        const std::string key = tune_key(R, lvl, T, nF, P.nsrc, filt);
+        const std::string key = tune_key(R, lvl, T, nF, P.nsrc, filt, P.mode);
         auto it = E.tune.find(key);
         if (it != E.tune.end()) {
             cr = count_with(it->second.tile, it->second.wm, false);
@@ -557,6 +578,15 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
         else k_wcoj_write<false><<<(unsigned)grid, kJoinThreads, 0, E.stream>>>(P);
     };
 
+    if (dmode) {
+        const uint64_t* d = E.readback(cr.dg.p, 3);
+        if (d[2]) throw Error(DL_ERR_STATE, "a row lies outside its relation's dense domain");
+        E.join_rows += d[0];
+        out.dense_rows += d[0];
+        out.dense_sunk = true;
+        E.phase_end(0);
+        return;
+    }
     if (last && count_sink) {
         if (E.instances) {
             std::vector<uint64_t> d(3ull * E.instances);
@@ -745,6 +775,7 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, co
     if (!place_filters(R, nsrc, J.lf, filter_levels)) return;   // a comparison that never holds
     J.plan = make_plan(R, src, filter_levels);
     J.count_sink = head.sink == DL_SINK_COUNT;
+    J.dense_sink = head.dense && head.dense_dirty && !J.count_sink;
     out.sorted_unique = head_is_order(R);
 
     LevelParams& P = J.base;

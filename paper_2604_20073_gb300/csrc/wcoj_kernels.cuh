@@ -8,7 +8,7 @@ constexpr int kJoinThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint8_t kVirtual = 0xff;   // source = the entry's sibling run in the frontier
 
-enum { MODE_FRONTIER = 0, MODE_HEAD = 1, MODE_COUNT = 2 };
+enum { MODE_FRONTIER = 0, MODE_HEAD = 1, MODE_COUNT = 2, MODE_DENSE = 3 };
 // A comparison applied at a level: relation of the level's value v to the other operand.
 enum { F_LT = 0, F_LE = 1, F_GT = 2, F_GE = 3, F_NE = 4 };
 constexpr int kMaxNeg = DL_MAX_NEG;
@@ -54,7 +54,16 @@ struct LevelParams {
     int8_t head_shared;                   // MODE_COUNT: leading head columns shared by an entry's siblings
     uint32_t head_const[kMaxArity];
     uint32_t* ocol[kMaxArity];
-    unsigned long long* digest;           // MODE_COUNT: [count, sum, xor]
+    unsigned long long* digest;           // MODE_COUNT: [count, sum, xor]; MODE_DENSE: [rows, new, bad]
+    // MODE_DENSE: the head relation's dense bitmap; a row's bit is sum over head columns c of
+    // value * dense_mul[c] (value < dense_dom[c]); the level's variable contributes
+    // v * dense_lvl_mul (v < dense_lvl_dom), the other columns come from the entry
+    uint32_t* dense_bits;
+    uint8_t* dense_dirty;
+    unsigned long long dense_mul[kMaxArity];
+    uint32_t dense_dom[kMaxArity];
+    unsigned long long dense_lvl_mul;
+    uint32_t dense_lvl_dom;
     // filters whose last variable is this level's (comparisons, negated atoms)
     uint32_t ncmp, nneg;
     uint8_t cmp_op[kMaxCmp];              // F_*: v op w
@@ -207,6 +216,19 @@ __device__ __forceinline__ uint32_t value_at(const LevelParams& P, const Unit& U
     return pos == (int)P.level ? U.v : __ldg(P.fval[pos] + U.e);
 }
 
+// MODE_DENSE: test-and-set bit idx of the head relation's bitmap; 1 if this call set it.  Bits
+// only go from 0 to 1 during the pass, so a set bit read from L2 settles the row without the
+// atomic (most derived rows of a projecting rule are duplicates).  A newly set bit marks its
+// block dirty for the round's extraction.
+__device__ __forceinline__ uint32_t dense_claim(const LevelParams& P, uint64_t idx) {
+    uint32_t* w = P.dense_bits + (idx >> 5);
+    const uint32_t m = 1u << (idx & 31);
+    if (__ldcg(w) & m) return 0u;
+    if (atomicOr(w, m) & m) return 0u;
+    P.dense_dirty[idx >> (5 + kDenseBlockShift)] = 1;
+    return 1u;
+}
+
 __device__ __forceinline__ void tile_bounds(const LevelParams& P, uint64_t& lo, uint64_t& hi) {
     if (P.naive) {
         const uint64_t e = blockIdx.x;
@@ -254,7 +276,8 @@ __device__ __forceinline__ void tile_entries(const LevelParams& P, uint64_t tlo,
     e1 = s_e1;
 }
 
-template <bool F>
+// D: MODE_DENSE (every survivor's row is test-and-set in the head relation's bitmap).
+template <bool F, bool D>
 __global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count(const __grid_constant__ LevelParams P) {
     uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
@@ -264,7 +287,18 @@ __global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count(const __grid_con
     for (uint64_t u = tlo + threadIdx.x; u < thi; u += blockDim.x) {
         if (!eval_unit<F>(P, u, e0, e1, U)) continue;
         cnt++;
-        if (P.mode == MODE_COUNT) {
+        if (D) {
+            uint64_t idx = 0;
+            bool in = true;
+            for (uint32_t c = 0; c < P.head_arity; c++) {
+                const int pos = P.head_pos[c];
+                const uint32_t x = pos < 0 ? P.head_const[c] : value_at(P, U, pos);
+                in = in && x < P.dense_dom[c];
+                idx += (unsigned long long)x * P.dense_mul[c];
+            }
+            if (in) hs += dense_claim(P, idx);
+            else hx = 1;   // a row outside the dense domain
+        } else if (P.mode == MODE_COUNT) {
             uint64_t h = kTupleHashSeed;
             for (uint32_t c = 0; c < P.head_arity; c++) {
                 const int pos = P.head_pos[c];
@@ -275,7 +309,15 @@ __global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count(const __grid_con
         }
     }
     const unsigned long long total = block_sum(cnt);
-    if (P.mode == MODE_COUNT) {
+    if (D) {
+        const unsigned long long s = block_sum(hs);
+        const int bad = __syncthreads_or(hx != 0);
+        if (threadIdx.x == 0 && total) {
+            atomicAdd(&P.digest[0], total);
+            atomicAdd(&P.digest[1], s);
+            if (bad) atomicOr(&P.digest[2], 1ull);
+        }
+    } else if (P.mode == MODE_COUNT) {
         const unsigned long long s = block_sum(hs);
 #pragma unroll
         for (int o = 16; o; o >>= 1) hx ^= __shfl_xor_sync(kFull, hx, o);
@@ -544,7 +586,8 @@ __device__ __forceinline__ uint32_t head_value(const LevelParams& P, int c, uint
     return pos < 0 ? P.head_const[c] : __ldg(P.fval[pos] + e);
 }
 
-template <int NS, bool F>
+// D: MODE_DENSE (every survivor's row is test-and-set in the head relation's bitmap).
+template <int NS, bool F, bool D>
 __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm(const __grid_constant__ LevelParams P) {
     const int lane = threadIdx.x & 31;
     // the warp's range lives in shared memory between entries (registers are the limit here)
@@ -565,7 +608,8 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
         uint64_t e = upper_bound_u64((const uint64_t*)P.C, 0, P.nF, s_wlo[threadIdx.x >> 5]);
         EntryState<NS> S;
         uint32_t r = 0;
-        uint64_t hpre = 0;        // MODE_COUNT: row hash over the head columns before head_lvl
+        uint64_t hpre = 0;        // MODE_COUNT: row hash over the head columns before head_lvl;
+                                  // MODE_DENSE: the entry's part of the bit index (~0: outside)
         // hash of the columns shared by the current sibling run, and that run (warp-uniform,
         // kept in shared memory: registers are the limit here)
         __shared__ unsigned long long s_hsh[kWarps];
@@ -575,7 +619,17 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
         for (;;) {
             const uint64_t wlo = s_wlo[threadIdx.x >> 5], whi = s_whi[threadIdx.x >> 5];
             const uint32_t stop = (uint32_t)(min(entry_load(P, S, e, wlo), whi) - wlo);
-            if (P.mode == MODE_COUNT) {
+            if (D) {
+                uint64_t ip = 0;
+                bool in = true;
+                for (uint32_t c = 0; c < P.head_arity; c++) {
+                    if (P.head_pos[c] == (int)P.level) continue;
+                    const uint32_t x = head_value(P, c, e);
+                    in = in && x < P.dense_dom[c];
+                    ip += (unsigned long long)x * P.dense_mul[c];
+                }
+                hpre = in ? ip : ~0ull;
+            } else if (P.mode == MODE_COUNT) {
                 int c0 = 0;
                 if (P.head_shared > 0) {
                     const uint32_t g = __ldg(P.seg + e);
@@ -602,7 +656,10 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
                 if (rr >= stop || !entry_eval(P, S, rr + S.eoff, v, nlo, nhi, dnlo, dnhi)) continue;
                 if (F && !filters_pass(P, e, v)) continue;
                 cnt++;
-                if (P.mode == MODE_COUNT) {
+                if (D) {
+                    if (hpre == ~0ull || v >= P.dense_lvl_dom) hx = 1;   // a row outside the dense domain
+                    else hs += dense_claim(P, hpre + (unsigned long long)v * P.dense_lvl_mul);
+                } else if (P.mode == MODE_COUNT) {
                     uint64_t h = tuple_hash_step(hpre, v, P.head_lvl);
                     for (uint32_t c = P.head_lvl + 1; c < P.head_arity; c++) h = tuple_hash_step(h, head_value(P, c, e), c);
                     hs += h;
@@ -620,11 +677,16 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 8 : 4) k_wcoj_count_wm
     for (int o = 16; o; o >>= 1) {
         cnt += __shfl_xor_sync(kFull, cnt, o);
         hs += __shfl_xor_sync(kFull, hs, o);
-        hx ^= __shfl_xor_sync(kFull, hx, o);
+        if (D) hx |= __shfl_xor_sync(kFull, hx, o);
+        else hx ^= __shfl_xor_sync(kFull, hx, o);
     }
     if (lane == 0) {
         P.block_count[(uint64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)] = cnt;
-        if (P.mode == MODE_COUNT && cnt) {
+        if (D && cnt) {
+            atomicAdd(&P.digest[0], (unsigned long long)cnt);
+            atomicAdd(&P.digest[1], hs);
+            if (hx) atomicOr(&P.digest[2], 1ull);
+        } else if (P.mode == MODE_COUNT && cnt) {
             atomicAdd(&P.digest[0], (unsigned long long)cnt);
             atomicAdd(&P.digest[1], hs);
             atomicXor(&P.digest[2], hx);
@@ -695,19 +757,30 @@ __global__ void __launch_bounds__(kJoinThreads, NS <= 2 ? 6 : 4) k_wcoj_write_wm
     }
 }
 
-#define DL_NS_DISPATCH_F(KERNEL, NSRC, F, GRID, STREAM, PARAMS)                                     \
+#define DL_NS_DISPATCH_F(KERNEL, NSRC, GRID, STREAM, PARAMS, ...)                                   \
     do {                                                                                            \
-        if ((NSRC) <= 1) KERNEL<1, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);               \
-        else if ((NSRC) <= 2) KERNEL<2, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);          \
-        else if ((NSRC) <= 3) KERNEL<3, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);          \
-        else if ((NSRC) <= 4) KERNEL<4, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);          \
-        else KERNEL<kMaxSrc + 1, F><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);                \
+        if ((NSRC) <= 1) KERNEL<1, __VA_ARGS__><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);     \
+        else if ((NSRC) <= 2) KERNEL<2, __VA_ARGS__><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS); \
+        else if ((NSRC) <= 3) KERNEL<3, __VA_ARGS__><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS); \
+        else if ((NSRC) <= 4) KERNEL<4, __VA_ARGS__><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS); \
+        else KERNEL<kMaxSrc + 1, __VA_ARGS__><<<(GRID), kJoinThreads, 0, (STREAM)>>>(PARAMS);      \
     } while (0)
 // by source count and by whether the level has filters
 #define DL_NS_DISPATCH(KERNEL, NSRC, FILT, GRID, STREAM, PARAMS)                                    \
     do {                                                                                            \
-        if (FILT) DL_NS_DISPATCH_F(KERNEL, NSRC, true, GRID, STREAM, PARAMS);                       \
-        else DL_NS_DISPATCH_F(KERNEL, NSRC, false, GRID, STREAM, PARAMS);                           \
+        if (FILT) DL_NS_DISPATCH_F(KERNEL, NSRC, GRID, STREAM, PARAMS, true);                       \
+        else DL_NS_DISPATCH_F(KERNEL, NSRC, GRID, STREAM, PARAMS, false);                           \
+    } while (0)
+// the count kernels: also by MODE_DENSE
+#define DL_NS_DISPATCH_D(KERNEL, NSRC, FILT, D, GRID, STREAM, PARAMS)                               \
+    do {                                                                                            \
+        if (D) {                                                                                    \
+            if (FILT) DL_NS_DISPATCH_F(KERNEL, NSRC, GRID, STREAM, PARAMS, true, true);             \
+            else DL_NS_DISPATCH_F(KERNEL, NSRC, GRID, STREAM, PARAMS, false, true);                 \
+        } else {                                                                                    \
+            if (FILT) DL_NS_DISPATCH_F(KERNEL, NSRC, GRID, STREAM, PARAMS, true, false);            \
+            else DL_NS_DISPATCH_F(KERNEL, NSRC, GRID, STREAM, PARAMS, false, false);                \
+        }                                                                                           \
     } while (0)
 
 // Sibling runs of a frontier: seg[k] = 1 if entry k starts a new parent's run.
