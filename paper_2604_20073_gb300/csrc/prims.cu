@@ -465,71 +465,125 @@ __global__ void k_dense_set(const __grid_constant__ TableView t, const __grid_co
     }
 }
 
-// Dense extraction, one warp per block of kDenseBlockWords words (8 per lane): the bits set in
-// `bits` but not in `old`.  Count pass: per block; clean blocks count 0.
+// Dense extraction: the bits set in `bits` but not in `old`.  A warp takes a group of 32
+// consecutive blocks of kDenseBlockWords words: lane l reads block l's dirty byte, and the warp
+// walks the dirty blocks of the group in order, 8 words per lane.  Count pass: per group.
 constexpr int kExtractWarps = 8;
 constexpr int kWordsPerLane = (int)(kDenseBlockWords / 32);
 
-__global__ void k_dense_block_count(const uint32_t* __restrict__ bits, const uint32_t* __restrict__ old,
-                                    const uint8_t* __restrict__ dirty, uint64_t nwords, uint64_t nblocks,
-                                    uint64_t* __restrict__ bcnt) {
-    const uint64_t b = blockIdx.x * (uint64_t)kExtractWarps + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= nblocks) return;
-    uint32_t c = 0;
-    if (dirty[b]) {
-        const uint64_t w0 = b * kDenseBlockWords + (uint64_t)lane * kWordsPerLane;
-#pragma unroll
-        for (int k = 0; k < kWordsPerLane; k++)
-            if (w0 + k < nwords) c += __popc(bits[w0 + k] & ~old[w0 + k]);
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) bcnt[b] = c;
-}
-
-// Write pass: each lane writes its words' new rows in bit order (its offset from an exclusive
-// warp scan of the lanes' counts), decoding the mixed-radix index into columns; then the
-// block's old words take the current bits and the block is clean again.
-__global__ void k_dense_block_write(const uint32_t* __restrict__ bits, uint32_t* __restrict__ old,
-                                    uint8_t* __restrict__ dirty, uint64_t nwords, uint64_t nblocks,
-                                    const uint64_t* __restrict__ boff, const __grid_constant__ DenseDom D,
-                                    const __grid_constant__ TableView out) {
-    const uint64_t b = blockIdx.x * (uint64_t)kExtractWarps + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= nblocks || !dirty[b]) return;
-    const uint64_t w0 = b * kDenseBlockWords + (uint64_t)lane * kWordsPerLane;
-    uint32_t nw[kWordsPerLane];
+__device__ __forceinline__ uint32_t block_new_words(const uint32_t* __restrict__ bits, const uint32_t* __restrict__ old,
+                                                    uint64_t w0, uint64_t nwords, uint32_t (&nw)[kWordsPerLane]) {
     uint32_t c = 0;
 #pragma unroll
     for (int k = 0; k < kWordsPerLane; k++) {
         nw[k] = w0 + k < nwords ? bits[w0 + k] & ~old[w0 + k] : 0u;
         c += __popc(nw[k]);
     }
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+    return c;
+}
+
+__global__ void k_dense_group_count(const uint32_t* __restrict__ bits, const uint32_t* __restrict__ old,
+                                    const uint8_t* __restrict__ dirty, uint64_t nwords, uint64_t nblocks,
+                                    uint64_t ngroups, uint64_t* __restrict__ gcnt) {
+    const uint64_t g = blockIdx.x * (uint64_t)kExtractWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= ngroups) return;
+    const uint64_t b0 = g * 32;
+    uint32_t m = __ballot_sync(0xffffffffu, b0 + lane < nblocks && dirty[b0 + lane]);
+    uint32_t c = 0;
+    while (m) {
+        const uint64_t b = b0 + (uint64_t)(__ffs(m) - 1);
+        m &= m - 1;
+        uint32_t nw[kWordsPerLane];
+        c += block_new_words(bits, old, b * kDenseBlockWords + (uint64_t)lane * kWordsPerLane, nwords, nw);
     }
-    uint64_t at = boff[b] + (incl - c);
 #pragma unroll
-    for (int k = 0; k < kWordsPerLane; k++) {
-        uint32_t m = nw[k];
-        while (m) {
-            const int bit = __ffs(m) - 1;
-            m &= m - 1;
-            uint64_t idx = (w0 + k) * 32 + (uint64_t)bit;
-            for (int col = (int)D.arity - 1; col >= 0; col--) {
-                out.col[col][at] = (uint32_t)(idx % D.d[col]);
-                idx /= D.d[col];
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) gcnt[g] = c;
+}
+
+// Write pass: per dirty block, 32 words at a time (word k of the step on lane k): the step's
+// new rows are dealt out in bit order, row p to lane p mod 32, so consecutive lanes store
+// consecutive rows (coalesced).  The lane of row p is found by a search over the lanes'
+// exclusive counts, the bit by its rank in that lane's word; the word's first index is
+// decoded into columns once (mixed radix) and the bit's offset added with carries.  Then the
+// block's old words take the current bits and the block is clean again.
+__global__ void k_dense_group_write(const uint32_t* __restrict__ bits, uint32_t* __restrict__ old,
+                                    uint8_t* __restrict__ dirty, uint64_t nwords, uint64_t nblocks, uint64_t ngroups,
+                                    const uint64_t* __restrict__ goff, const __grid_constant__ DenseDom D,
+                                    const __grid_constant__ TableView out) {
+    const uint64_t g = blockIdx.x * (uint64_t)kExtractWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= ngroups) return;
+    const uint64_t b0 = g * 32;
+    const bool mine = b0 + lane < nblocks && dirty[b0 + lane];
+    uint32_t m = __ballot_sync(0xffffffffu, mine);
+    uint64_t run = goff[g];
+    while (m) {
+        const uint64_t b = b0 + (uint64_t)(__ffs(m) - 1);
+        m &= m - 1;
+        for (int step = 0; step < kWordsPerLane; step++) {
+            const uint64_t w = b * kDenseBlockWords + (uint64_t)step * 32 + lane;
+            const uint32_t x = w < nwords ? bits[w] & ~old[w] : 0u;
+            const uint32_t c = __popc(x);
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            at++;
+            const uint32_t excl = incl - c, n = __shfl_sync(0xffffffffu, incl, 31);
+            if (n == 0) continue;
+            if (x) old[w] |= x;
+            // the lane's word's first bit index, as columns (columns at and above D.arity: 0)
+            uint32_t dig[kMaxArity];
+            {
+                uint64_t q = w * 32;
+#pragma unroll
+                for (int col = kMaxArity - 1; col >= 0; col--) {
+                    dig[col] = 0;
+                    if (col < (int)D.arity) {
+                        dig[col] = (uint32_t)(q % D.d[col]);
+                        q /= D.d[col];
+                    }
+                }
+            }
+            for (uint32_t j = 0; j < n; j += 32) {
+                const uint32_t p = j + lane;
+                // source lane: the last lane whose exclusive count is <= p
+                int src = 0;
+#pragma unroll
+                for (int h = 16; h; h >>= 1) {
+                    const uint32_t e = __shfl_sync(0xffffffffu, excl, src + h);
+                    if (e <= p) src += h;
+                }
+                const uint32_t xs = __shfl_sync(0xffffffffu, x, src);
+                const uint32_t k = p - __shfl_sync(0xffffffffu, excl, src);
+                uint32_t add = p < n ? (uint32_t)__fns(xs, 0, (int)k + 1) : 0u;
+                uint32_t v[kMaxArity];
+#pragma unroll
+                for (int col = 0; col < kMaxArity; col++) v[col] = __shfl_sync(0xffffffffu, dig[col], src);
+#pragma unroll
+                for (int col = kMaxArity - 1; col >= 0; col--) {
+                    if (col >= (int)D.arity || !add) continue;
+                    uint64_t t = (uint64_t)v[col] + add;
+                    add = 0;
+                    while (t >= D.d[col]) {
+                        t -= D.d[col];
+                        add++;
+                    }
+                    v[col] = (uint32_t)t;
+                }
+                if (p < n) {
+#pragma unroll
+                    for (int col = 0; col < kMaxArity; col++)
+                        if (col < (int)D.arity) out.col[col][run + p] = v[col];
+                }
+            }
+            run += n;
         }
-        if (w0 + k < nwords) old[w0 + k] |= nw[k];
     }
-    __syncwarp();
-    if (lane == 0) dirty[b] = 0;
+    if (mine) dirty[b0 + lane] = 0;
 }
 
 // Test-and-set every row's bit: a row is new iff its bit was clear (it is neither in the
@@ -637,6 +691,16 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
     const uint64_t i0 = split[blockIdx.x], i1 = split[blockIdx.x + 1];
     const uint64_t j0 = d0 - i0;
     const uint32_t na = (uint32_t)(i1 - i0), n = (uint32_t)(d1 - d0), nb = n - na;
+    if (na == 0 || nb == 0) {
+        // the tile comes from one side only (the common case when a small delta is merged into
+        // a large relation): a straight coalesced copy
+        for (uint32_t c = 0; c < arity; c++) {
+            const uint32_t* src = na ? a.col[c] + i0 : b.col[c] + j0;
+            uint32_t* oc = out.col[c] + d0;
+            for (uint32_t t = threadIdx.x; t < n; t += kMergeThreads) oc[t] = src[t];
+        }
+        return;
+    }
     for (uint32_t c = 0; c < arity; c++) {
         const uint32_t* ac = a.col[c] + i0;
         const uint32_t* bc = b.col[c] + j0;
@@ -974,22 +1038,23 @@ uint64_t dense_extract(Engine& E, uint32_t arity, const uint32_t* dom, const uin
     D.arity = arity;
     for (uint32_t c = 0; c < arity; c++) D.d[c] = dom[c];
     const uint64_t nblocks = (nwords + kDenseBlockWords - 1) / kDenseBlockWords;
-    const uint64_t grid = (nblocks + kExtractWarps - 1) / kExtractWarps;
+    const uint64_t ngroups = (nblocks + 31) / 32;
+    const uint64_t grid = (ngroups + kExtractWarps - 1) / kExtractWarps;
     if (grid >= (1ull << 31)) throw Error(DL_ERR_CAPACITY, "dense bitmap too large to extract");
-    auto bcnt = E.array<uint64_t>(nblocks + 1);
+    auto gcnt = E.array<uint64_t>(ngroups + 1);
     {
         KernelScope ks(E, DL_K_DELTA, nblocks);
-        k_dense_block_count<<<(unsigned)grid, 32 * kExtractWarps, 0, E.stream>>>(bits, old, dirty, nwords, nblocks,
-                                                                                 bcnt.p);
+        k_dense_group_count<<<(unsigned)grid, 32 * kExtractWarps, 0, E.stream>>>(bits, old, dirty, nwords, nblocks,
+                                                                                 ngroups, gcnt.p);
         DL_CHECK_LAUNCH();
     }
-    scan_u64(E, bcnt.p, nblocks, false, bcnt.p + nblocks);
-    const uint64_t total = E.readback(bcnt.p + nblocks, 1)[0];
+    scan_u64(E, gcnt.p, ngroups, false, gcnt.p + ngroups);
+    const uint64_t total = E.readback(gcnt.p + ngroups, 1)[0];
     const TableView out = alloc_out(total);
     if (total) {
-        KernelScope ks(E, DL_K_DELTA, 4ull * arity * total);
-        k_dense_block_write<<<(unsigned)grid, 32 * kExtractWarps, 0, E.stream>>>(bits, old, dirty, nwords, nblocks,
-                                                                                 bcnt.p, D, out);
+        KernelScope ks(E, DL_K_DELTA, nblocks + 4ull * arity * total);
+        k_dense_group_write<<<(unsigned)grid, 32 * kExtractWarps, 0, E.stream>>>(bits, old, dirty, nwords, nblocks,
+                                                                                 ngroups, gcnt.p, D, out);
         DL_CHECK_LAUNCH();
     }
     return total;
