@@ -675,9 +675,11 @@ __global__ void k_merge_splits(const __grid_constant__ TableView a, const __grid
 }
 
 // One CTA per kMergeTile output rows: the CTA stages the a- and b-windows between its two
-// splits in shared memory with coalesced loads, each thread merges its kMergeItems outputs
-// from shared memory into a staged output tile, and the tile is written back with coalesced
-// stores (every input and output row crosses HBM once).
+// splits in shared memory with coalesced loads (each thread's loads of a column issued
+// before its stores), each thread merges its kMergeItems outputs from shared memory and
+// records the staged row each output takes (2 bytes, not the row: a smaller footprint keeps
+// more CTAs resident), and the tile is written back with coalesced stores through those
+// indexes (every input and output row crosses HBM once).
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__ TableView a,
                                                          const __grid_constant__ TableView b,
                                                          const __grid_constant__ TableView out,
@@ -685,7 +687,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
     extern __shared__ uint32_t smem[];
     const uint32_t arity = a.arity;
     uint32_t* sin = smem;                                  // arity x kMergeTile: a-window, then b-window
-    uint32_t* sout = smem + (size_t)arity * kMergeTile;    // arity x kMergeTile: merged tile
+    uint16_t* sidx = (uint16_t*)(smem + (size_t)arity * kMergeTile);   // kMergeTile: staged row of each output
     const uint64_t total = a.n + b.n;
     const uint64_t d0 = (uint64_t)blockIdx.x * kMergeTile, d1 = min(d0 + kMergeTile, total);
     const uint64_t i0 = split[blockIdx.x], i1 = split[blockIdx.x + 1];
@@ -704,8 +706,17 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
     for (uint32_t c = 0; c < arity; c++) {
         const uint32_t* ac = a.col[c] + i0;
         const uint32_t* bc = b.col[c] + j0;
-        for (uint32_t t = threadIdx.x; t < n; t += kMergeThreads)
-            sin[c * kMergeTile + t] = t < na ? ac[t] : bc[t - na];
+        uint32_t r[kMergeItems];
+#pragma unroll
+        for (int k = 0; k < kMergeItems; k++) {
+            const uint32_t t = threadIdx.x + (uint32_t)k * kMergeThreads;
+            r[k] = t < na ? ac[t] : t < n ? bc[t - na] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kMergeItems; k++) {
+            const uint32_t t = threadIdx.x + (uint32_t)k * kMergeThreads;
+            if (t < n) sin[c * kMergeTile + t] = r[k];
+        }
     }
     __syncthreads();
     const uint32_t dd = min((uint32_t)threadIdx.x * kMergeItems, n);
@@ -718,13 +729,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__
     const uint32_t end = min(dd + kMergeItems, n);
     for (uint32_t k = dd; k < end; k++) {
         const bool take_a = ib >= nb || (ia < na && !staged_less(sin, arity, na + ib, ia));
-        const uint32_t src = take_a ? ia++ : na + ib++;
-        for (uint32_t c = 0; c < arity; c++) sout[c * kMergeTile + k] = sin[c * kMergeTile + src];
+        sidx[k] = (uint16_t)(take_a ? ia++ : na + ib++);
     }
     __syncthreads();
     for (uint32_t c = 0; c < arity; c++) {
         uint32_t* oc = out.col[c] + d0;
-        for (uint32_t t = threadIdx.x; t < n; t += kMergeThreads) oc[t] = sout[c * kMergeTile + t];
+        for (uint32_t t = threadIdx.x; t < n; t += kMergeThreads) oc[t] = sin[c * kMergeTile + sidx[t]];
     }
 }
 
@@ -1120,7 +1130,7 @@ uint64_t anti_filter(Engine& E, const TableView& in, const AtomView& full, const
 void merge_rows(Engine& E, const TableView& a, const TableView& b, const TableView& out) {
     const uint64_t total = a.n + b.n;
     if (!total) return;
-    const size_t smem = sizeof(uint32_t) * 2ull * a.arity * kMergeTile;
+    const size_t smem = sizeof(uint32_t) * a.arity * kMergeTile + sizeof(uint16_t) * kMergeTile;
     // the kernel's dynamic shared memory limit, raised once per device (setting it twice is harmless)
     static std::atomic<uint64_t> attr_set{0};
     const uint64_t bit = 1ull << (E.device & 63);
