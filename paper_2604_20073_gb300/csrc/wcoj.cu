@@ -136,10 +136,13 @@ Plan make_plan(const Rule& R, const std::vector<const Index*>& idx, uint64_t fil
 // Units per CTA tile for a level of T units.  Each warp starts with a search for its first
 // entry, which larger tiles amortise; at least eight waves of resident CTAs (8 per SM) keep
 // the tail of the launch short.
-uint32_t auto_tile(const Engine& E, uint64_t T) {
+uint32_t auto_tile(const Engine& E, uint64_t T, uint64_t nF, bool warp_major) {
     const uint64_t waves = 8ull * 8ull * E.sms;
     uint32_t t = 4096;
     while (t < (1u << 16) && T / (2ull * t) >= waves) t *= 2;
+    // a thread per unit: keep a tile's entries within the shared-memory stage of entry ends
+    if (!warp_major)
+        while (t > 4096 && (long double)t * nF > (long double)kStageC * T) t >>= 1;
     return t;
 }
 
@@ -563,9 +566,10 @@ void JoinRun::level(uint32_t lvl, const Frontier& F, uint64_t ea, uint64_t eb) {
         tuned = true;
     }
     if (!tuned) {
-        const uint32_t tile = E.tile_units ? E.tile_units : auto_tile(E, T);
         // warp-major kernels when entries average >= 32 units (one count per warp)
-        cr = count_with(tile, !P.naive && T >= 32 * nF, false);
+        const bool wmk = !P.naive && T >= 32 * nF;
+        const uint32_t tile = E.tile_units ? E.tile_units : auto_tile(E, T, nF, wmk);
+        cr = count_with(tile, wmk, false);
     }
     P.tile = cr.tile;
     P.block_count = (unsigned long long*)cr.bc.p;

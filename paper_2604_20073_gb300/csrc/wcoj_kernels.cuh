@@ -156,13 +156,28 @@ struct Unit {
 };
 
 // Decode unit u of the flat space into (entry, local) and evaluate it (F: the level has
-// filters).
+// filters).  sC: the tile's entry ends staged in shared memory (sC[0] = the unit before entry
+// e0, sC[1 + i] = C[e0 + i]), or null to search C in global memory.
 template <bool F>
-__device__ __forceinline__ bool eval_unit(const LevelParams& P, uint64_t u, uint64_t e0, uint64_t e1, Unit& U) {
-    uint64_t e;
-    if (P.naive) e = e0;
-    else e = upper_bound_u64((const uint64_t*)P.C, e0, e1, u);
-    const uint64_t local = u - (e ? P.C[e - 1] : 0);
+__device__ __forceinline__ bool eval_unit(const LevelParams& P, uint64_t u, uint64_t e0, uint64_t e1,
+                                          const unsigned long long* sC, Unit& U) {
+    uint64_t e, prev;
+    if (P.naive) {
+        e = e0;
+        prev = e ? P.C[e - 1] : 0;
+    } else if (sC) {
+        uint32_t lo = 0, hi = (uint32_t)(e1 - e0);
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (sC[1 + mid] <= u) lo = mid + 1; else hi = mid;
+        }
+        e = e0 + lo;
+        prev = sC[lo];
+    } else {
+        e = upper_bound_u64((const uint64_t*)P.C, e0, e1, u);
+        prev = e ? P.C[e - 1] : 0;
+    }
+    const uint64_t local = u - prev;
     U.e = e;
     const int s0 = P.drv[e];
     uint32_t v, d_lo, d_hi;   // the driving source's narrowed range for v
@@ -217,13 +232,15 @@ __device__ __forceinline__ uint32_t value_at(const LevelParams& P, const Unit& U
 }
 
 // MODE_DENSE: test-and-set bit idx of the head relation's bitmap; 1 if this call set it.  Bits
-// only go from 0 to 1 during the pass, so a set bit read from L2 settles the row without the
-// atomic (most derived rows of a projecting rule are duplicates).  A newly set bit marks its
-// block dirty for the round's extraction.
+// only go from 0 to 1 during the stratum, so a set bit read through the non-coherent cached
+// path settles the row without the atomic (most derived rows of a projecting rule are
+// duplicates, and neighbouring entries hit the same words in L1); a stale clear bit only
+// sends the row on to the atomic, which decides.  A newly set bit marks its block dirty for
+// the round's extraction.
 __device__ __forceinline__ uint32_t dense_claim(const LevelParams& P, uint64_t idx) {
     uint32_t* w = P.dense_bits + (idx >> 5);
     const uint32_t m = 1u << (idx & 31);
-    if (__ldcg(w) & m) return 0u;
+    if (__ldg(w) & m) return 0u;
     if (atomicOr(w, m) & m) return 0u;
     P.dense_dirty[idx >> (5 + kDenseBlockShift)] = 1;
     return 1u;
@@ -257,6 +274,20 @@ __device__ __forceinline__ T block_sum(T v) {
     return t;  // valid in thread 0
 }
 
+// A tile's entry ends staged in shared memory when the tile spans at most kStageC entries
+// (the per-unit decode then searches shared memory instead of chasing C through L1/L2);
+// returns null otherwise.  Every thread of the CTA calls it (it synchronises).
+constexpr uint32_t kStageC = 3072;
+__device__ __forceinline__ const unsigned long long* stage_entry_ends(const LevelParams& P, uint64_t e0, uint64_t e1,
+                                                                      unsigned long long* buf) {
+    if (P.naive || e1 - e0 > kStageC) return nullptr;
+    const uint32_t ne = (uint32_t)(e1 - e0);
+    for (uint32_t i = threadIdx.x; i <= ne; i += blockDim.x)
+        buf[i] = i ? P.C[e0 + i - 1] : (e0 ? P.C[e0 - 1] : 0ull);
+    __syncthreads();
+    return buf;
+}
+
 __device__ __forceinline__ void tile_entries(const LevelParams& P, uint64_t tlo, uint64_t thi, uint64_t& e0,
                                              uint64_t& e1) {
     __shared__ uint64_t s_e0, s_e1;
@@ -282,10 +313,12 @@ __global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count(const __grid_con
     uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
     tile_entries(P, tlo, thi, e0, e1);
+    __shared__ unsigned long long s_ends[kStageC + 1];
+    const unsigned long long* sC = stage_entry_ends(P, e0, e1, s_ends);
     unsigned long long cnt = 0, hs = 0, hx = 0;
     Unit U;
     for (uint64_t u = tlo + threadIdx.x; u < thi; u += blockDim.x) {
-        if (!eval_unit<F>(P, u, e0, e1, U)) continue;
+        if (!eval_unit<F>(P, u, e0, e1, sC, U)) continue;
         cnt++;
         if (D) {
             uint64_t idx = 0;
@@ -338,10 +371,12 @@ __global__ void __launch_bounds__(kJoinThreads, 8) k_wcoj_count_inst(const __gri
     uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
     tile_entries(P, tlo, thi, e0, e1);
+    __shared__ unsigned long long s_ends[kStageC + 1];
+    const unsigned long long* sC = stage_entry_ends(P, e0, e1, s_ends);
     unsigned long long cnt = 0;
     Unit U;
     for (uint64_t u = tlo + threadIdx.x; u < thi; u += blockDim.x) {
-        if (!eval_unit<F>(P, u, e0, e1, U)) continue;
+        if (!eval_unit<F>(P, u, e0, e1, sC, U)) continue;
         cnt++;
         uint64_t h = kTupleHashSeed;
         for (uint32_t c = 1; c < P.head_arity; c++) {
@@ -389,11 +424,13 @@ __global__ void __launch_bounds__(kJoinThreads, 4) k_wcoj_write(const __grid_con
     uint64_t tlo, thi, e0, e1;
     tile_bounds(P, tlo, thi);
     tile_entries(P, tlo, thi, e0, e1);
+    __shared__ unsigned long long s_ends[kStageC + 1];
+    const unsigned long long* sC = stage_entry_ends(P, e0, e1, s_ends);
     uint64_t run = P.block_count[P.tile_base + blockIdx.x] - P.out_base;
     Unit U;
     for (uint64_t base = tlo; base < thi; base += blockDim.x) {
         const uint64_t u = base + threadIdx.x;
-        const uint32_t f = (u < thi && eval_unit<F>(P, u, e0, e1, U)) ? 1u : 0u;
+        const uint32_t f = (u < thi && eval_unit<F>(P, u, e0, e1, sC, U)) ? 1u : 0u;
         uint32_t total;
         const uint32_t pos = block_exclusive_scan_u32(f, total);
         if (f) {
