@@ -428,7 +428,8 @@ int dl_decode_unit(const uint64_t* C, const uint64_t* d2, uint64_t K, uint64_t g
  * work of concurrent requests overlaps on the device, in the spirit of the stream-parallel
  * rule schedule of Section 6), and keep their relations resident on the device until the
  * client releases them.  A request that outgrows its share fails alone with
- * DL_ERR_CAPACITY; others are not disturbed.  The paper evaluates one program at a time;
+ * DL_ERR_CAPACITY; others are not disturbed.  With dl_server_config.grow_retries the server
+ * instead re-runs it with a doubled share, so callers need not know final sizes up front.  The paper evaluates one program at a time;
  * this loop is an addition for serving many programs. */
 typedef struct dl_server dl_server;
 
@@ -438,6 +439,10 @@ typedef struct dl_server_config {
     uint32_t max_slots;       /* concurrent requests (worker threads / streams); 0 = 8 */
     uint32_t flags;           /* DL_FLAG_* for every request's engine */
     uint64_t default_share;   /* share of a request that states none; 0 = 1 GiB */
+    uint32_t grow_retries;    /* final sizes unknown up front: a request that fails with
+                                 DL_ERR_CAPACITY is evaluated again from scratch with twice its
+                                 share (at most the whole budget), re-queued ahead of later
+                                 arrivals, up to this many times; 0 = never (it fails alone) */
 } dl_server_config;
 
 typedef struct dl_rule_spec {  /* a rule of a request, as dl_rule_add_ex takes it */
@@ -478,6 +483,7 @@ typedef struct dl_server_stats {
     uint64_t submitted, admitted, completed, failed;
     uint64_t reserved_bytes, peak_reserved_bytes;
     uint32_t running, queued;
+    uint64_t regrown;         /* re-evaluations with a doubled share (dl_server_config.grow_retries) */
 } dl_server_stats;
 
 /* Create / destroy a server (destroy waits for running requests and frees everything). */

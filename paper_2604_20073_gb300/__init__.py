@@ -87,7 +87,7 @@ class dl_stats(ctypes.Structure):
 
 class dl_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("default_share", ctypes.c_uint64)]
+                ("flags", ctypes.c_uint32), ("default_share", ctypes.c_uint64), ("grow_retries", ctypes.c_uint32)]
 
 
 class dl_rule_spec(ctypes.Structure):
@@ -110,7 +110,8 @@ class dl_request(ctypes.Structure):
 class dl_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("failed", ctypes.c_uint64), ("reserved_bytes", ctypes.c_uint64),
-                ("peak_reserved_bytes", ctypes.c_uint64), ("running", ctypes.c_uint32), ("queued", ctypes.c_uint32)]
+                ("peak_reserved_bytes", ctypes.c_uint64), ("running", ctypes.c_uint32), ("queued", ctypes.c_uint32),
+                ("regrown", ctypes.c_uint64)]
 
 
 DL_REQ_QUEUED, DL_REQ_RUNNING, DL_REQ_DONE = 0, 1, 2
@@ -545,12 +546,12 @@ class Server:
     until released."""
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, max_slots: int = 8, flags: int = 0,
-                 default_share: int = 0):
+                 default_share: int = 0, grow_retries: int = 0):
         import torch
         self.lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the Datalog server runs only on the GPU")
-        cfg = dl_server_config(device, budget_bytes, max_slots, flags, default_share)
+        cfg = dl_server_config(device, budget_bytes, max_slots, flags, default_share, grow_retries)
         h = ctypes.c_void_p()
         rc = self.lib.dl_server_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != DL_OK:

@@ -41,6 +41,7 @@ struct Ticket {
     std::vector<RuleCopy> rules;
     std::vector<FactCopy> facts;
     uint64_t share = 0;
+    uint32_t grows = 0;               // re-evaluations with a doubled share so far
     bool admitted = false;            // its share was added to the server's reservation
     int state = DL_REQ_QUEUED;
     int status = DL_OK;
@@ -53,6 +54,7 @@ struct dl_server {
     int device = 0;
     uint64_t budget = 0, reserved = 0, peak_reserved = 0, default_share = 1ull << 30;
     uint32_t flags = 0;
+    uint32_t grow_retries = 0;
     cudaMemPool_t pool = nullptr;
     std::mutex mu;
     std::condition_variable cv;
@@ -62,7 +64,7 @@ struct dl_server {
     std::unordered_map<uint64_t, std::unique_ptr<Ticket>> tickets;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
-    uint64_t submitted = 0, admitted = 0, completed = 0, failed = 0;
+    uint64_t submitted = 0, admitted = 0, completed = 0, failed = 0, regrown = 0;
     uint32_t running = 0;
 };
 
@@ -110,8 +112,10 @@ int evaluate(dl_server* s, cudaStream_t stream, Ticket* t) {
     }
     for (FactCopy& f : t->facts)
         if ((rc = dl_load_facts_rows(e, f.rel, f.rows.data(), f.nrows)) != DL_OK) return rc;
-    t->facts.clear();
-    t->facts.shrink_to_fit();
+    if (t->grows >= s->grow_retries) {   // no re-evaluation can follow: drop the host copy
+        t->facts.clear();
+        t->facts.shrink_to_fit();
+    }
     return dl_fixpoint(e, nullptr);
 }
 
@@ -144,13 +148,30 @@ void worker_loop(dl_server* s, size_t slot) {
             t->state = DL_REQ_RUNNING;
         }
         const int rc = evaluate(s, stream, t);
+        // outgrew its share: start again from scratch with twice the share, ahead of later
+        // arrivals (the failed engine's memory goes back to the pool first)
+        const bool regrow = rc == DL_ERR_CAPACITY && t->grows < s->grow_retries && t->share < s->budget;
+        if (regrow && t->eng) {
+            dl_engine_destroy(t->eng);
+            t->eng = nullptr;
+        }
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            t->status = rc;
-            t->state = DL_REQ_DONE;
             s->running--;
-            s->completed++;
-            if (rc != DL_OK) s->failed++;
+            if (regrow) {
+                s->reserved -= t->share;
+                t->admitted = false;
+                t->share = std::min(s->budget, 2 * t->share);
+                t->grows++;
+                t->state = DL_REQ_QUEUED;
+                s->queue.push_front(t);
+                s->regrown++;
+            } else {
+                t->status = rc;
+                t->state = DL_REQ_DONE;
+                s->completed++;
+                if (rc != DL_OK) s->failed++;
+            }
         }
         s->cv.notify_all();
     }
@@ -179,6 +200,7 @@ int dl_server_create(const dl_server_config* cfg, dl_server** out) {
     s->budget = c.budget_bytes ? c.budget_bytes : (uint64_t)(fr * 0.9);
     s->flags = c.flags;
     if (c.default_share) s->default_share = c.default_share;
+    s->grow_retries = c.grow_retries;
     cudaMemPoolProps props;
     memset(&props, 0, sizeof(props));
     props.allocType = cudaMemAllocationTypePinned;
@@ -334,6 +356,7 @@ int dl_server_get_stats(dl_server* s, dl_server_stats* out) {
     out->peak_reserved_bytes = s->peak_reserved;
     out->running = s->running;
     out->queued = (uint32_t)s->queue.size();
+    out->regrown = s->regrown;
     return DL_OK;
 }
 

@@ -2,7 +2,7 @@
 to a server with few slots and a small memory budget (so requests queue, are admitted as
 slots and memory free up, and run concurrently on separate streams).  Every result equals
 the oracle's and the same request evaluated alone; a request that outgrows its share fails
-alone with DL_ERR_CAPACITY."""
+alone with DL_ERR_CAPACITY, or, with grow_retries, is evaluated again with a doubled share."""
 import threading
 import time
 
@@ -108,6 +108,30 @@ def test_over_share_request_fails_alone():
         srv.release(ok)
         with pytest.raises(pkg.DatalogError):
             srv.submit(P.TC_TRI_RELS, {"E": small}, P.TC_TRI, share=4 << 30)
+
+
+def test_share_grows_until_the_request_fits():
+    """Final sizes unknown up front: with grow_retries the request that fails at an 8 MiB share
+    is evaluated again with twice the share until it fits, while another request runs; both
+    equal the oracle, and the doubled shares are returned to the budget."""
+    e = dg.rmat_edges(4096, 32768, 1000)
+    small = dg.rmat_edges(256, 2000, 3)
+    with pkg.Server(budget_bytes=2 << 30, max_slots=2, grow_retries=12) as srv:
+        big = srv.submit(P.TC_TRI_RELS, {"E": e}, P.TC_TRI, share=8 << 20)
+        ok = srv.submit(P.TC_TRI_RELS, {"E": small}, P.TC_TRI, share=256 << 20)
+        assert srv.wait(big) == pkg.DL_OK
+        assert srv.wait(ok) == pkg.DL_OK
+        for t, facts in ((big, {"E": e}), (ok, {"E": small})):
+            ref = oracle.evaluate(P.TC_TRI_RELS, facts, P.TC_TRI)
+            eng = srv.result(t)
+            for name in P.TC_TRI_RELS:
+                assert np.array_equal(eng.fetch(name), ref.relations[name]), name
+            assert sorted(eng.strata()) == sorted(ref.strata)
+        st = srv.stats()
+        assert st["regrown"] >= 1 and st["failed"] == 0 and st["completed"] == 2
+        srv.release(big)
+        srv.release(ok)
+        assert srv.stats()["reserved_bytes"] == 0
 
 
 def test_served_rules_with_negation_and_comparisons():
