@@ -121,8 +121,11 @@ typedef struct dl_config {
                                  8 x this many bits gets one bit per possible row; a round's new
                                  rows are then found by one test-and-set per derived row (paper
                                  Section 4, Compute Delta), replacing the probe of the relation's
-                                 index and the deduplicating sort.  At most a quarter of the
-                                 budget left.  0 = default (8 GiB), 1 = never */
+                                 index and the deduplicating sort.  By default the join sets the
+                                 bits itself and the round's delta is read back from them (see
+                                 DL_FLAG_NO_DENSE_SINK), which keeps a second copy of the bitmap:
+                                 then at most an eighth of the budget left, else a quarter.
+                                 0 = default (8 GiB), 1 = never */
     const char* tune_cache;   /* DL_FLAG_AUTOTUNE: text file of tuned choices, read when the
                                  engine is created (if it exists) and rewritten when it is
                                  destroyed or by dl_tune_save; NULL = choices kept in memory */
