@@ -223,8 +223,12 @@ typedef struct dl_atom {
  * (x1..xm)"; it fixes the attribute order of the join, not a filter on values).
  * var_order must be a permutation of the distinct body variables.  Every head variable
  * must occur in the body (range restriction).
- * GPU path limits: constants in body atoms, and a variable repeated within one body atom,
- * return DL_ERR_UNSUPPORTED; head constants are allowed.
+ * A constant in a body atom, or a variable repeated within one body atom, selects the rows
+ * whose column equals it: each such term becomes a fresh variable with two comparisons that
+ * make it equal to the constant or to the variable's first occurrence (the fresh variable of
+ * a constant leads the variable order, a repeat's follows its variable), so each one takes
+ * one of DL_MAX_VARS and two of DL_MAX_CMP (DL_ERR_UNSUPPORTED beyond).  Head constants are
+ * allowed.  A count sink's rule takes no body constants or repeats.
  * Errors: DL_ERR_ARG (bad ids, arity mismatch, unsafe head, bad order, nbody == 0 or
  * > DL_MAX_BODY, more than DL_MAX_VARS variables), DL_ERR_UNSUPPORTED, DL_ERR_STATE. */
 int dl_rule_add(dl_engine* e, const dl_atom* head, const dl_atom* body, uint32_t nbody,

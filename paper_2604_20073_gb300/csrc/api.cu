@@ -1375,12 +1375,51 @@ Rule parse_rule(Engine& E, const dl_atom* head, const dl_atom* body, uint32_t nb
     if (!var_order || nvars != bvars.size()) throw Error(DL_ERR_ARG, "variable order must list every body variable once");
     std::set<uint32_t> ord(var_order, var_order + nvars);
     if (ord != bvars) throw Error(DL_ERR_ARG, "variable order is not a permutation of the body variables");
-    if (unsupported_const) throw Error(DL_ERR_UNSUPPORTED, "constants in body atoms are not supported on the GPU path");
-    if (unsupported_repeat)
-        throw Error(DL_ERR_UNSUPPORTED, "a variable repeated within one body atom is not supported on the GPU path");
     if (neg_unsupported)
         throw Error(DL_ERR_UNSUPPORTED, "negated atoms take distinct variables only on the GPU path");
     r.order.assign(var_order, var_order + nvars);
+    if (unsupported_const || unsupported_repeat) {
+        // A constant or a repeated variable in a body atom becomes a fresh variable f with the
+        // comparisons f <= t and t <= f (equality; t the constant or the first occurrence),
+        // checked at f's level: a constant's f leads the variable order (its level keeps only
+        // that value of the column), a repeat's f follows its variable.  Same bindings.
+        uint32_t next = 1024;   // user variable ids are below 1024
+        std::vector<uint32_t> lead;
+        std::vector<std::pair<uint32_t, uint32_t>> after;   // (fresh, original)
+        for (RuleAtom& ra : r.body) {
+            std::set<uint32_t> here;
+            for (uint32_t c = 0; c < ra.arity; c++) {
+                dl_term& t = ra.terms[c];
+                const bool is_const = t.kind == DL_TERM_CONST;
+                if (!is_const && here.insert(t.id).second) continue;
+                const uint32_t f = next++;
+                RuleCmp le1, le2;
+                le1.op = le2.op = DL_CMP_LE;
+                le1.a.kind = DL_TERM_VAR;
+                le1.a.id = f;
+                le1.b = t;
+                le2.a = t;
+                le2.b = le1.a;
+                r.cmps.push_back(le1);
+                r.cmps.push_back(le2);
+                if (is_const) lead.push_back(f);
+                else after.push_back({f, t.id});
+                t.kind = DL_TERM_VAR;
+                t.id = f;
+            }
+        }
+        std::vector<uint32_t> order(lead);
+        for (uint32_t v : r.order) {
+            order.push_back(v);
+            for (auto& fa : after)
+                if (fa.second == v) order.push_back(fa.first);
+        }
+        r.order = order;
+        if (r.order.size() + (E.instances ? 1 : 0) > DL_MAX_VARS)
+            throw Error(DL_ERR_UNSUPPORTED, "too many variables once body constants and repeats are rewritten");
+        if (r.cmps.size() > DL_MAX_CMP)
+            throw Error(DL_ERR_UNSUPPORTED, "too many comparisons once body constants and repeats are rewritten");
+    }
     if (E.instances) {
         // batched form: the instance id is column 0 of every atom and the first join variable
         const uint32_t inst_var = 0x7fffffffu;
