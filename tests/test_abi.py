@@ -105,3 +105,39 @@ def test_engine_create_fails_cleanly_without_gpu(lib):
     assert rc == pkg.DL_ERR_CUDA and not h.value
     with pytest.raises(RuntimeError):
         pkg.Engine()
+
+
+STRUCTS = ["dl_config", "dl_term", "dl_cmp", "dl_atom", "dl_kernel_stat", "dl_stats", "dl_server_config",
+           "dl_rule_spec", "dl_fact_spec", "dl_request", "dl_server_stats"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the ctypes binding mirrors has the header's size and field offsets (a C
+    program built here against include/dl.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dl.h"', "int main(void) {"]
+    for name in STRUCTS:
+        st = getattr(pkg, name)
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    want = {}
+    for line in out:
+        if line.strip():
+            name, field, value = line.split()
+            want[(name, field)] = int(value)
+    for name in STRUCTS:
+        st = getattr(pkg, name)
+        assert ctypes.sizeof(st) == want[(name, "sizeof")], name
+        for field, _ in st._fields_:
+            assert getattr(st, field).offset == want[(name, field)], (name, field)
