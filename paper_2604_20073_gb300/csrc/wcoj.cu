@@ -799,7 +799,7 @@ void run_join(Engine& E, const Rule& R, const std::vector<const Index*>& src, co
             P.head_pos[c] = (int8_t)(std::find(R.order.begin(), R.order.end(), R.head.terms[c].id) - R.order.begin());
         }
     }
-    for (uint32_t a = 0; a < J.plan.natoms; a++) P.lazy_pos[a] = (int8_t)J.plan.lazy_pos[a];
+    for (uint32_t a = 0; a < J.plan.natoms && a < (uint32_t)kMaxAtoms; a++) P.lazy_pos[a] = (int8_t)J.plan.lazy_pos[a];
     Frontier root;   // the empty prefix
     J.level(0, root, 0, 1);
 }
